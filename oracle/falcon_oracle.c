@@ -1,0 +1,605 @@
+/*
+ * falcon_oracle.c -- plain, slow CPU oracle of the Falcon codec
+ * (Falcon: GPU-Based Floating-point Adaptive Lossless Compression, arXiv 2511.04140).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path links, loads or calls this
+ * file; only the test-suite, the smoke check and the CPU-baseline leg of the bench do.
+ * It shares no code, header, table or constant generator with the CUDA library: the
+ * powers of ten come from the C library's correctly rounded decimal parser (strtod /
+ * strtof), the arithmetic is plain IEEE FP64/FP32 compiled with -ffp-contract=off.
+ *
+ * Every function follows one passage of the paper, in the paper's order and notation:
+ *   - Def. 1/2, Eq. 2 (Sec. 2.2)            decimal place alpha, decimal significand beta
+ *   - Alg. 2 (Sec. 3.2.2), Thm 4            DPAndDSCalculation
+ *   - Sec. 3.2.3, Eq. 4, Thm 5              digit transformation (Case 1 / Case 2)
+ *   - Eq. 5                                 delta + zigzag
+ *   - Sec. 3.3, Fig. 8                      adaptive sparse/dense bit-plane encoding,
+ *                                           chunk record layout
+ *   - Sec. 3.4, Alg. 3                      size array + concatenated chunk records
+ *   - Sec. 4                                decompression = exact inverse
+ *
+ * Readings where the paper is silent (numbered as in the design notes):
+ *   R1  -0.0, NaN (any payload), +-inf and subnormals are exceptions (alpha,beta)=(23,16)
+ *       (FP32: (11,8)); they force the chunk to Case 2 (bit-exact through BinLong).
+ *   R3  floor(log10|v|) := the largest k with |v| >= fl(10^k) (fl = correctly rounded).
+ *   R4  the product v (x) 10^alpha is the IEEE multiply, no contraction.
+ *   R5  round() is half-away-from-zero (ties cannot occur where it matters).
+ *   R6  a Case-1 chunk is additionally checked value by value: g_i / 10^alpha_max must
+ *       reproduce v_i bit for bit, otherwise the chunk falls back to Case 2.
+ *   R7  integer arithmetic is modulo 2^64 (2^32 for FP32); zigzag uses an arithmetic
+ *       shift; z_1 is stored raw, little-endian, 8 bytes (FP32: 4).
+ *   R8  row 1 of the transposed matrix is the most significant plane (bit w-1).
+ *   R9  bits are MSB-first everywhere: column 8j+i -> bit 7-i of row byte j; bitmap bit
+ *       for row byte j -> bit 7-(j%8) of bitmap byte j/8; the flag bits of rows 1..w are
+ *       the last w bits of ceil(w/8) bytes read MSB-first; 0 = sparse, 1 = dense.
+ *   R10 sparse iff lambda > cols/64; a tie is stored dense.
+ *   R11 a chunk of m values has cols = round_up(m-1, 64) columns; missing columns are
+ *       zero pads that count in bytes, bitmap and lambda but not in w. m = 1 -> w = 0.
+ *   R12 a Case-2 record stores the sentinels (alpha,beta_hat) = (23,16) (FP32: (11,8));
+ *       a decoder treats a record as Case 1 iff alpha <= 22 and beta_hat <= 15
+ *       (FP32: alpha <= 10, beta_hat <= 7).
+ *   R13 the u32 size array precedes the records.
+ *   R14 FP32: alpha <= 10, beta <= 7, mu = |x| * 2^-23, x = v * 10^alpha computed exactly
+ *       (in FP64), round trip and decode are fl32((float)g / (float)10^alpha).
+ *
+ * Stream layout (little-endian):
+ *   0  "FLCN"  4  version=1 (u8)  5  dtype (u8: 0=f64, 1=f32)  6  reserved u16 = 0
+ *   8  block_size u32   12 reserved u32 = 0   16 n u64   24 num_chunks u64
+ *   32 u32 size[num_chunks]   then the chunk records, concatenated.
+ * Chunk record: [alpha_max u8][beta_hat_max u8][z_1: 8 B (f32: 4 B)][w u8]
+ *               [flags: ceil(w/8) B][row 1] ... [row w]
+ */
+#include <stdint.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <stdio.h>
+#include <string.h>
+#include <math.h>
+
+enum { OR_F64 = 0, OR_F32 = 1 };
+enum { OR_OK = 0, OR_ERR_INVALID = 1, OR_ERR_CAPACITY = 2, OR_ERR_CORRUPT = 3 };
+
+#define OR_HEADER_BYTES 32u
+#define OR_MAX_BLOCK 65537u
+
+/* ------------------------------------------------------------------------------------ */
+/* Powers of ten, correctly rounded, from the C library's decimal parser.               */
+/* ------------------------------------------------------------------------------------ */
+#define P10_LO (-350)
+#define P10_HI 330
+static double p10_64[P10_HI - P10_LO + 1];
+static float p10_32[P10_HI - P10_LO + 1];
+static int p10_ready = 0;
+
+static void init_p10(void)
+{
+    if (p10_ready) return;
+    char buf[32];
+    for (int k = P10_LO; k <= P10_HI; ++k) {
+        snprintf(buf, sizeof buf, "1e%d", k);
+        p10_64[k - P10_LO] = strtod(buf, NULL);
+        p10_32[k - P10_LO] = strtof(buf, NULL);
+    }
+    p10_ready = 1;
+}
+
+/* fl(10^k) in FP64 / FP32 */
+double oracle_pow10_f64(int k) { init_p10(); return p10_64[k - P10_LO]; }
+float oracle_pow10_f32(int k) { init_p10(); return p10_32[k - P10_LO]; }
+
+/* ------------------------------------------------------------------------------------ */
+/* Bit views                                                                            */
+/* ------------------------------------------------------------------------------------ */
+static uint64_t bits64(double v) { uint64_t u; memcpy(&u, &v, 8); return u; }
+static double from_bits64(uint64_t u) { double v; memcpy(&v, &u, 8); return v; }
+static uint32_t bits32(float v) { uint32_t u; memcpy(&u, &v, 4); return u; }
+static float from_bits32(uint32_t u) { float v; memcpy(&v, &u, 4); return v; }
+
+/* R1: special numbers (footnote of Sec. 2.1) are treated as exceptions. */
+int oracle_is_special_f64(double v)
+{
+    uint64_t u = bits64(v);
+    uint64_t e = (u >> 52) & 0x7FF;
+    if (e == 0x7FF) return 1;                     /* NaN (any payload), +-inf */
+    if (e == 0 && (u << 1) != 0) return 1;        /* subnormal */
+    if (u == 0x8000000000000000ull) return 1;     /* -0.0 */
+    return 0;
+}
+
+int oracle_is_special_f32(float v)
+{
+    uint32_t u = bits32(v);
+    uint32_t e = (u >> 23) & 0xFF;
+    if (e == 0xFF) return 1;
+    if (e == 0 && (u << 1) != 0) return 1;
+    if (u == 0x80000000u) return 1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* R3: floor(log10|v|) as the largest k with |v| >= fl(10^k). a > 0, finite, normal.    */
+/* The libm estimate is only a starting point; the table decides.                      */
+/* ------------------------------------------------------------------------------------ */
+int oracle_floor_log10_f64(double a)
+{
+    init_p10();
+    int k = (int)floor(log10(a));
+    if (k < P10_LO + 2) k = P10_LO + 2;
+    if (k > P10_HI - 2) k = P10_HI - 2;
+    while (a < oracle_pow10_f64(k)) --k;
+    while (a >= oracle_pow10_f64(k + 1)) ++k;
+    return k;
+}
+
+int oracle_floor_log10_f32(float a)
+{
+    init_p10();
+    int k = (int)floor(log10((double)a));
+    if (k < P10_LO + 2) k = P10_LO + 2;
+    if (k > P10_HI - 2) k = P10_HI - 2;
+    while (a < oracle_pow10_f32(k)) --k;
+    while (a >= oracle_pow10_f32(k + 1)) ++k;
+    return k;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Alg. 2 DPAndDSCalculation(v) (Sec. 3.2.2): enumerate alpha from 0, stop at the first */
+/* alpha with eps <= mu (Thm 4), verify the round trip (otherwise exception (23,16)).   */
+/* Loop while beta <= 15 and alpha <= 22. alpha > 22 or beta > 15 means exception.      */
+/* ------------------------------------------------------------------------------------ */
+void oracle_dp_ds_f64(double v, int *alpha, int *beta)
+{
+    if (oracle_is_special_f64(v)) { *alpha = 23; *beta = 16; return; }   /* R1 */
+    if (v == 0.0) { *alpha = 0; *beta = 0; return; }                     /* special case */
+    int a = 0;
+    int b = a + oracle_floor_log10_f64(fabs(v)) + 1;                    /* Eq. 2 */
+    while (b <= 15 && a <= 22) {
+        double x = v * oracle_pow10_f64(a);                             /* v (x) 10^alpha */
+        double r = round(x);
+        if (fabs(x - r) <= fabs(x) * 0x1p-52) {                         /* eps <= mu */
+            if (r / oracle_pow10_f64(a) != v) { a = 23; b = 16; }       /* round trip */
+            break;
+        }
+        a = a + 1;
+        b = b + 1;
+    }
+    *alpha = a;
+    *beta = b;
+}
+
+/* FP32 analogue (R14): alpha <= 10, beta <= 7, mu = |x| * 2^-23, x exact in FP64. */
+void oracle_dp_ds_f32(float v, int *alpha, int *beta)
+{
+    if (oracle_is_special_f32(v)) { *alpha = 11; *beta = 8; return; }
+    if (v == 0.0f) { *alpha = 0; *beta = 0; return; }
+    int a = 0;
+    int b = a + oracle_floor_log10_f32(fabsf(v)) + 1;
+    while (b <= 7 && a <= 10) {
+        double x = (double)v * (double)oracle_pow10_f32(a);            /* exact */
+        double r = round(x);
+        if (fabs(x - r) <= fabs(x) * 0x1p-23) {
+            if ((float)r / oracle_pow10_f32(a) != v) { a = 11; b = 8; }
+            break;
+        }
+        a = a + 1;
+        b = b + 1;
+    }
+    *alpha = a;
+    *beta = b;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Zigzag (Eq. 5): Zigzag(x) = (x << 1) xor (x >> 63), arithmetic shift (R7).           */
+/* ------------------------------------------------------------------------------------ */
+uint64_t oracle_zigzag64(uint64_t x)
+{
+    return (x << 1) ^ (uint64_t)((int64_t)x >> 63);
+}
+uint64_t oracle_unzigzag64(uint64_t z)
+{
+    return (z >> 1) ^ (0 - (z & 1));
+}
+uint32_t oracle_zigzag32(uint32_t x)
+{
+    return (x << 1) ^ (uint32_t)((int32_t)x >> 31);
+}
+uint32_t oracle_unzigzag32(uint32_t z)
+{
+    return (z >> 1) ^ (0u - (z & 1u));
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Digit transformation of one chunk (Sec. 3.2.3, Eq. 4, Thm 5, Alg. 3 integer part).   */
+/* Output: alpha_max, beta_hat_max as stored (R12 sentinels in Case 2), case flag, and  */
+/* G = {g_1..g_m} as raw 64-bit words (FP32: low 32 bits).                               */
+/* Returns the number of R6 firings (values that failed the Case-1 round trip).        */
+/* ------------------------------------------------------------------------------------ */
+int oracle_chunk_transform(const void *vals, uint32_t m, int dtype,
+                           int *alpha_max_out, int *beta_hat_out, int *case1_out,
+                           uint64_t *g)
+{
+    int r6_firings = 0;
+    if (dtype == OR_F64) {
+        const double *v = (const double *)vals;
+        /* alpha_max = max DP(v_i) via Alg. 2; v_max = max |v_i| */
+        int alpha_max = 0;
+        int any_exception = 0;
+        double v_max = 0.0;
+        for (uint32_t i = 0; i < m; ++i) {
+            int a, b;
+            oracle_dp_ds_f64(v[i], &a, &b);
+            if (a > alpha_max) alpha_max = a;
+            if (a > 22 || b > 15) any_exception = 1;
+        }
+        /* beta_hat_max = alpha_max + floor(log10 v_max) + 1 (0 if v_max = 0); only
+           meaningful when no value is special, i.e. alpha_max <= 22. */
+        int beta_hat = 16;
+        if (alpha_max <= 22) {
+            for (uint32_t i = 0; i < m; ++i) {
+                double av = fabs(v[i]);
+                if (av > v_max) v_max = av;
+            }
+            beta_hat = (v_max == 0.0) ? 0 : alpha_max + oracle_floor_log10_f64(v_max) + 1;
+        }
+        int case1 = (alpha_max <= 22 && beta_hat <= 15);
+        /* An exception value always forces alpha_max > 22 or beta_hat > 15 (Eq. 2). The
+           oracle checks it explicitly instead of relying on that argument. */
+        if (any_exception) case1 = 0;
+        if (case1) {
+            double p = oracle_pow10_f64(alpha_max);
+            for (uint32_t i = 0; i < m; ++i) {
+                double x = v[i] * p;                     /* v_i (x) 10^alpha_max */
+                int64_t gi = (int64_t)llround(x);        /* g_i = round(...) */
+                g[i] = (uint64_t)gi;
+                double back = (double)gi / p;            /* Thm 5: g_i / 10^alpha_max */
+                if (bits64(back) != bits64(v[i])) ++r6_firings;
+            }
+            if (r6_firings) case1 = 0;                   /* R6 */
+        }
+        if (!case1) {
+            for (uint32_t i = 0; i < m; ++i)
+                g[i] = oracle_zigzag64(bits64(v[i])); /* g_i = Zigzag(BinLong(v_i)) */
+            alpha_max = 23;
+            beta_hat = 16;
+        }
+        *alpha_max_out = alpha_max;
+        *beta_hat_out = beta_hat;
+        *case1_out = case1;
+    } else {
+        const float *v = (const float *)vals;
+        int alpha_max = 0;
+        int any_exception = 0;
+        for (uint32_t i = 0; i < m; ++i) {
+            int a, b;
+            oracle_dp_ds_f32(v[i], &a, &b);
+            if (a > alpha_max) alpha_max = a;
+            if (a > 10 || b > 7) any_exception = 1;
+        }
+        int beta_hat = 8;
+        if (alpha_max <= 10) {
+            float v_max = 0.0f;
+            for (uint32_t i = 0; i < m; ++i) {
+                float av = fabsf(v[i]);
+                if (av > v_max) v_max = av;
+            }
+            beta_hat = (v_max == 0.0f) ? 0 : alpha_max + oracle_floor_log10_f32(v_max) + 1;
+        }
+        int case1 = (alpha_max <= 10 && beta_hat <= 7);
+        if (any_exception) case1 = 0;
+        if (case1) {
+            float p = oracle_pow10_f32(alpha_max);
+            for (uint32_t i = 0; i < m; ++i) {
+                double x = (double)v[i] * (double)p;     /* exact (R14) */
+                int32_t gi = (int32_t)llround(x);
+                g[i] = (uint64_t)(uint32_t)gi;
+                float back = (float)gi / p;
+                if (bits32(back) != bits32(v[i])) ++r6_firings;
+            }
+            if (r6_firings) case1 = 0;
+        }
+        if (!case1) {
+            for (uint32_t i = 0; i < m; ++i)
+                g[i] = (uint64_t)oracle_zigzag32(bits32(v[i]));
+            alpha_max = 11;
+            beta_hat = 8;
+        }
+        *alpha_max_out = alpha_max;
+        *beta_hat_out = beta_hat;
+        *case1_out = case1;
+    }
+    return r6_firings;
+}
+
+/* Eq. 5: z_1 = g_1, z_i = Zigzag(g_i - g_{i-1}) for i > 1 (modulo 2^64 / 2^32). */
+void oracle_delta_zigzag(const uint64_t *g, uint32_t m, int dtype, uint64_t *z)
+{
+    for (uint32_t i = 0; i < m; ++i) {
+        if (i == 0) {
+            z[i] = g[0];
+        } else if (dtype == OR_F64) {
+            z[i] = oracle_zigzag64(g[i] - g[i - 1]);
+        } else {
+            z[i] = (uint64_t)oracle_zigzag32((uint32_t)g[i] - (uint32_t)g[i - 1]);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Sec. 3.3 adaptive bit-plane encoding of Z \ {z_1} and the chunk record (Fig. 8c).    */
+/* ------------------------------------------------------------------------------------ */
+static int clz64(uint64_t x) { int n = 0; if (!x) return 64; while (!(x & 0x8000000000000000ull)) { x <<= 1; ++n; } return n; }
+
+/* cols = round_up(m - 1, 64) (R11) */
+static uint32_t chunk_cols(uint32_t m) { return m <= 1 ? 0 : ((m - 1 + 63) / 64) * 64; }
+
+/* Bit of z at plane p for column c (c indexes z_{c+2}; pad columns are 0). */
+static int plane_bit(const uint64_t *z, uint32_t m, uint32_t c, int p)
+{
+    uint32_t idx = c + 1;                 /* 0-based index of z_{c+2} */
+    if (idx >= m) return 0;               /* zero pad column (R11) */
+    return (int)((z[idx] >> p) & 1u);
+}
+
+/* Encodes one record; returns its byte length or 0 if it does not fit in cap. */
+size_t oracle_encode_z(const uint64_t *z, uint32_t m, int dtype, int alpha_max, int beta_hat,
+                       uint8_t *out, size_t cap)
+{
+    const int width = (dtype == OR_F64) ? 64 : 32;
+    const int z1_bytes = (dtype == OR_F64) ? 8 : 4;
+    const uint32_t cols = chunk_cols(m);
+    const uint32_t row_bytes = cols / 8;
+    const uint32_t bitmap_bytes = cols / 64;
+
+    /* w = width - min clz(z_2..z_m); clz(0) = width */
+    int lead_min = width;
+    for (uint32_t i = 1; i < m; ++i) {
+        int lead = clz64(z[i]) - (64 - width);
+        if (lead < lead_min) lead_min = lead;
+    }
+    const int w = width - lead_min;
+    const uint32_t flag_bytes = (uint32_t)(w + 7) / 8;
+
+    size_t pos = 0;
+#define PUT(byte) do { if (pos >= cap) return 0; out[pos++] = (uint8_t)(byte); } while (0)
+    PUT(alpha_max);
+    PUT(beta_hat);
+    for (int k = 0; k < z1_bytes; ++k) PUT((z[0] >> (8 * k)) & 0xFF);
+    PUT(w);
+    size_t flag_pos = pos;
+    for (uint32_t k = 0; k < flag_bytes; ++k) PUT(0);
+
+    uint8_t *row = (uint8_t *)malloc(row_bytes ? row_bytes : 1);
+    for (int r = 1; r <= w; ++r) {
+        int p = w - r;                            /* R8: row 1 = plane w-1 */
+        /* byte j holds columns 8j..8j+7, column 8j+i at bit 7-i (R9) */
+        uint32_t lambda = 0;
+        for (uint32_t j = 0; j < row_bytes; ++j) {
+            unsigned byte = 0;
+            for (int i = 0; i < 8; ++i)
+                byte |= (unsigned)plane_bit(z, m, 8 * j + i, p) << (7 - i);
+            row[j] = (uint8_t)byte;
+            if (byte == 0) ++lambda;              /* zero byte */
+        }
+        int sparse = lambda > cols / 64;          /* Sec. 3.3 criterion, tie -> dense (R10) */
+        /* flag: the last w bits of the flag bytes, row 1 first, MSB-first (R9) */
+        uint32_t bitpos = flag_bytes * 8 - (uint32_t)w + (uint32_t)(r - 1);
+        if (!sparse) out[flag_pos + bitpos / 8] |= (uint8_t)(0x80u >> (bitpos % 8));
+        if (sparse) {
+            for (uint32_t b = 0; b < bitmap_bytes; ++b) {
+                unsigned bm = 0;
+                for (int i = 0; i < 8; ++i)
+                    if (row[8 * b + i] != 0) bm |= 0x80u >> i;
+                if (pos >= cap) { free(row); return 0; }
+                out[pos++] = (uint8_t)bm;
+            }
+            for (uint32_t j = 0; j < row_bytes; ++j)
+                if (row[j] != 0) { if (pos >= cap) { free(row); return 0; } out[pos++] = row[j]; }
+        } else {
+            for (uint32_t j = 0; j < row_bytes; ++j) { if (pos >= cap) { free(row); return 0; } out[pos++] = row[j]; }
+        }
+    }
+    free(row);
+#undef PUT
+    return pos;
+}
+
+/* One chunk: Eq. 4 -> Eq. 5 -> Sec. 3.3. Returns the record length, 0 on overflow. */
+size_t oracle_encode_chunk(const void *vals, uint32_t m, int dtype, uint8_t *out, size_t cap)
+{
+    uint64_t *g = (uint64_t *)malloc(sizeof(uint64_t) * (m ? m : 1));
+    uint64_t *z = (uint64_t *)malloc(sizeof(uint64_t) * (m ? m : 1));
+    int alpha_max, beta_hat, case1;
+    oracle_chunk_transform(vals, m, dtype, &alpha_max, &beta_hat, &case1, g);
+    oracle_delta_zigzag(g, m, dtype, z);
+    size_t len = oracle_encode_z(z, m, dtype, alpha_max, beta_hat, out, cap);
+    free(g);
+    free(z);
+    return len;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Stream level (Sec. 3.4, Alg. 3): header, u32 size array (R13), records.            */
+/* ------------------------------------------------------------------------------------ */
+static uint64_t num_chunks_of(uint64_t n, uint32_t block) { return (n + block - 1) / block; }
+
+static size_t record_bound(uint32_t m, int dtype)
+{
+    const int width = (dtype == OR_F64) ? 64 : 32;
+    const int z1_bytes = (dtype == OR_F64) ? 8 : 4;
+    return 2 + (size_t)z1_bytes + 1 + (size_t)(width / 8) + (size_t)width * (chunk_cols(m) / 8);
+}
+
+size_t oracle_bound(uint64_t n, int dtype, uint32_t block)
+{
+    if ((dtype != OR_F64 && dtype != OR_F32) || block < 2 || block > OR_MAX_BLOCK) return 0;
+    uint64_t nc = num_chunks_of(n, block);
+    size_t total = OR_HEADER_BYTES + 4 * (size_t)nc;
+    if (nc == 0) return total;
+    total += (size_t)(nc - 1) * record_bound(block, dtype);
+    total += record_bound((uint32_t)(n - (nc - 1) * (uint64_t)block), dtype);
+    return total;
+}
+
+static void put_u32(uint8_t *p, uint32_t x) { for (int k = 0; k < 4; ++k) p[k] = (uint8_t)(x >> (8 * k)); }
+static void put_u64(uint8_t *p, uint64_t x) { for (int k = 0; k < 8; ++k) p[k] = (uint8_t)(x >> (8 * k)); }
+static uint32_t get_u32(const uint8_t *p) { uint32_t x = 0; for (int k = 3; k >= 0; --k) x = (x << 8) | p[k]; return x; }
+static uint64_t get_u64(const uint8_t *p) { uint64_t x = 0; for (int k = 7; k >= 0; --k) x = (x << 8) | p[k]; return x; }
+
+int oracle_compress(const void *in, uint64_t n, int dtype, uint32_t block,
+                    uint8_t *out, size_t cap, size_t *out_bytes)
+{
+    if ((dtype != OR_F64 && dtype != OR_F32) || block < 2 || block > OR_MAX_BLOCK) return OR_ERR_INVALID;
+    const size_t s = (dtype == OR_F64) ? 8 : 4;
+    const uint64_t nc = num_chunks_of(n, block);
+    const size_t data_start = OR_HEADER_BYTES + 4 * (size_t)nc;
+    if (cap < data_start) return OR_ERR_CAPACITY;
+    memcpy(out, "FLCN", 4);
+    out[4] = 1;
+    out[5] = (uint8_t)dtype;
+    out[6] = 0; out[7] = 0;
+    put_u32(out + 8, block);
+    put_u32(out + 12, 0);
+    put_u64(out + 16, n);
+    put_u64(out + 24, nc);
+    size_t pos = data_start;
+    for (uint64_t c = 0; c < nc; ++c) {
+        uint64_t first = c * block;
+        uint32_t m = (uint32_t)((n - first) < block ? (n - first) : block);
+        size_t len = oracle_encode_chunk((const uint8_t *)in + first * s, m, dtype, out + pos, cap - pos);
+        if (len == 0) return OR_ERR_CAPACITY;
+        put_u32(out + OR_HEADER_BYTES + 4 * c, (uint32_t)len);
+        pos += len;
+    }
+    *out_bytes = pos;
+    return OR_OK;
+}
+
+/* Parses a stream header. */
+int oracle_stream_info(const uint8_t *in, size_t in_bytes, uint64_t *n, int *dtype, uint32_t *block,
+                       uint64_t *num_chunks)
+{
+    if (in_bytes < OR_HEADER_BYTES) return OR_ERR_CORRUPT;
+    if (memcmp(in, "FLCN", 4) != 0 || in[4] != 1) return OR_ERR_CORRUPT;
+    int dt = in[5];
+    uint32_t b = get_u32(in + 8);
+    uint64_t nn = get_u64(in + 16);
+    uint64_t nc = get_u64(in + 24);
+    if (dt != OR_F64 && dt != OR_F32) return OR_ERR_CORRUPT;
+    if (b < 2 || b > OR_MAX_BLOCK) return OR_ERR_CORRUPT;
+    if (nc != num_chunks_of(nn, b)) return OR_ERR_CORRUPT;
+    *n = nn; *dtype = dt; *block = b; *num_chunks = nc;
+    return OR_OK;
+}
+
+/* Sec. 4: decode one record of m values. Returns OR_OK or OR_ERR_CORRUPT. */
+int oracle_decode_chunk(const uint8_t *rec, size_t len, uint32_t m, int dtype, void *vals)
+{
+    const int width = (dtype == OR_F64) ? 64 : 32;
+    const int z1_bytes = (dtype == OR_F64) ? 8 : 4;
+    const uint32_t cols = chunk_cols(m);
+    const uint32_t row_bytes = cols / 8;
+    const uint32_t bitmap_bytes = cols / 64;
+    size_t pos = 0;
+    if (len < (size_t)(3 + z1_bytes)) return OR_ERR_CORRUPT;
+    int alpha = rec[pos++];
+    int beta_hat = rec[pos++];
+    uint64_t z1 = 0;
+    for (int k = 0; k < z1_bytes; ++k) z1 |= (uint64_t)rec[pos++] << (8 * k);
+    int w = rec[pos++];
+    if (w > width) return OR_ERR_CORRUPT;
+    if (m <= 1 && w != 0) return OR_ERR_CORRUPT;
+    uint32_t flag_bytes = (uint32_t)(w + 7) / 8;
+    if (pos + flag_bytes > len) return OR_ERR_CORRUPT;
+    size_t flag_pos = pos;
+    pos += flag_bytes;
+
+    uint64_t *z = (uint64_t *)calloc(m ? m : 1, sizeof(uint64_t));
+    z[0] = z1;
+    for (int r = 1; r <= w; ++r) {
+        int p = w - r;
+        uint32_t bitpos = flag_bytes * 8 - (uint32_t)w + (uint32_t)(r - 1);
+        int dense = (rec[flag_pos + bitpos / 8] >> (7 - bitpos % 8)) & 1;
+        for (uint32_t j = 0; j < row_bytes; ++j) {
+            unsigned byte;
+            if (dense) {
+                if (pos + j >= len) { free(z); return OR_ERR_CORRUPT; }
+                byte = rec[pos + j];
+            } else {
+                /* bitmap then the non-zero bytes in row order */
+                if (pos + bitmap_bytes > len) { free(z); return OR_ERR_CORRUPT; }
+                int nz = (rec[pos + j / 8] >> (7 - j % 8)) & 1;
+                if (!nz) {
+                    byte = 0;
+                } else {
+                    uint32_t rank = 0;
+                    for (uint32_t q = 0; q < j; ++q) rank += (rec[pos + q / 8] >> (7 - q % 8)) & 1;
+                    if (pos + bitmap_bytes + rank >= len) { free(z); return OR_ERR_CORRUPT; }
+                    byte = rec[pos + bitmap_bytes + rank];
+                }
+            }
+            for (int i = 0; i < 8; ++i) {
+                uint32_t c = 8 * j + (uint32_t)i;
+                if (c + 1 < m && ((byte >> (7 - i)) & 1)) z[c + 1] |= (uint64_t)1 << p;
+            }
+        }
+        if (dense) {
+            pos += row_bytes;
+        } else {
+            uint32_t nnz = 0;
+            for (uint32_t q = 0; q < row_bytes; ++q) nnz += (rec[pos + q / 8] >> (7 - q % 8)) & 1;
+            pos += bitmap_bytes + nnz;
+        }
+        if (pos > len) { free(z); return OR_ERR_CORRUPT; }
+    }
+    if (pos != len) { free(z); return OR_ERR_CORRUPT; }
+
+    /* inverse of Eq. 5: g_1 = z_1, g_i = g_{i-1} + Unzigzag(z_i) */
+    if (dtype == OR_F64) {
+        int case1 = (alpha <= 22 && beta_hat <= 15);                /* R12 */
+        double *out = (double *)vals;
+        uint64_t g = z[0];
+        for (uint32_t i = 0; i < m; ++i) {
+            if (i > 0) g = g + oracle_unzigzag64(z[i]);
+            /* inverse of Eq. 4 */
+            if (case1) out[i] = (double)(int64_t)g / oracle_pow10_f64(alpha);
+            else out[i] = from_bits64(oracle_unzigzag64(g));
+        }
+    } else {
+        int case1 = (alpha <= 10 && beta_hat <= 7);
+        float *out = (float *)vals;
+        uint32_t g = (uint32_t)z[0];
+        for (uint32_t i = 0; i < m; ++i) {
+            if (i > 0) g = g + oracle_unzigzag32((uint32_t)z[i]);
+            if (case1) out[i] = (float)(int32_t)g / oracle_pow10_f32(alpha);
+            else out[i] = from_bits32(oracle_unzigzag32(g));
+        }
+    }
+    free(z);
+    return OR_OK;
+}
+
+int oracle_decompress(const uint8_t *in, size_t in_bytes, void *out, size_t out_cap_bytes,
+                      uint64_t *n_out)
+{
+    uint64_t n, nc;
+    int dtype;
+    uint32_t block;
+    int st = oracle_stream_info(in, in_bytes, &n, &dtype, &block, &nc);
+    if (st != OR_OK) return st;
+    const size_t s = (dtype == OR_F64) ? 8 : 4;
+    if (n > out_cap_bytes / s) return OR_ERR_CAPACITY;
+    size_t data_start = OR_HEADER_BYTES + 4 * (size_t)nc;
+    if (nc > (in_bytes - OR_HEADER_BYTES) / 4 || data_start > in_bytes) return OR_ERR_CORRUPT;
+    size_t pos = data_start;
+    for (uint64_t c = 0; c < nc; ++c) {
+        uint32_t len = get_u32(in + OR_HEADER_BYTES + 4 * c);
+        if (len > in_bytes - pos) return OR_ERR_CORRUPT;
+        uint64_t first = c * block;
+        uint32_t m = (uint32_t)((n - first) < block ? (n - first) : block);
+        st = oracle_decode_chunk(in + pos, len, m, dtype, (uint8_t *)out + first * s);
+        if (st != OR_OK) return st;
+        pos += len;
+    }
+    *n_out = n;
+    return OR_OK;
+}
