@@ -1,0 +1,126 @@
+/*
+ * falcon.h -- C ABI of libfalcon, a GB300 (sm_103a) implementation of the Falcon codec:
+ * lossless, per-chunk compression of FP64 / FP32 series (Falcon: GPU-Based Floating-point
+ * Adaptive Lossless Compression, arXiv 2511.04140).
+ *
+ * What one call computes (per chunk of block_size consecutive values):
+ *   - the float-to-integer transform of Sec. 3.2 (Alg. 2 decimal place detection, Eq. 4:
+ *     Case 1 g_i = round(v_i * 10^alpha_max) when alpha_max <= 22 and beta_hat_max <= 15,
+ *     verified to round-trip bit for bit; otherwise Case 2 g_i = Zigzag(BinLong(v_i)));
+ *   - delta + zigzag coding (Eq. 5);
+ *   - the adaptive sparse/dense bit-plane encoding of Sec. 3.3 (Fig. 8);
+ *   - the compressed-size synchronisation and chunk writing of Sec. 3.4 (Alg. 3), as a
+ *     single-pass decoupled look-back inside the kernel;
+ * and decompression (Sec. 4) is its exact inverse.  FP32 follows the same steps with
+ * alpha <= 10, beta <= 7 and 32-bit integers.
+ *
+ * Stream format (self-describing, little-endian):
+ *   bytes 0..31   "FLCN", version u8 (=1), dtype u8, u16 0, block_size u32, u32 0,
+ *                 n u64, num_chunks u64
+ *   then          u32 size[num_chunks]  (compressed bytes of each chunk record)
+ *   then          the chunk records back to back:
+ *                 [alpha_max u8][beta_hat_max u8][z_1: 8 B (FP32: 4 B)][w u8]
+ *                 [flags: ceil(w/8) B, the last w bits = rows 1..w, 1 = dense]
+ *                 [row 1 = bit plane w-1] ... [row w = bit plane 0]
+ *   A sparse row is a bitmap of cols/64 bytes (bit 7 of byte 0 = row byte 0) followed by
+ *   the row's non-zero bytes; a dense row is its cols/8 bytes; cols = round_up(m-1, 64)
+ *   for a chunk of m values.  Case-2 records carry alpha_max = 23, beta_hat_max = 16
+ *   (FP32: 11 and 8).
+ *
+ * Conventions for every entry point:
+ *   - Return value: a falcon_status.  Nothing is thrown across the ABI.  On error the
+ *     contents of output buffers are undefined.
+ *   - "d_" pointers are device pointers (cudaMalloc / torch CUDA storage) on the current
+ *     device; "h_" pointers are host pointers.  The caller owns every buffer it passes.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Value buffers must be aligned to the element size; stream buffers to 16 bytes.
+ *   - Supported block sizes on the GPU: 2 <= block_size <= 1025 (the paper's n = 1025 and
+ *     the 1024-value chunks are both in range).  Larger block sizes give
+ *     FALCON_ERR_UNSUPPORTED.
+ */
+#ifndef FALCON_H_
+#define FALCON_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FALCON_ABI_VERSION 1
+#define FALCON_HEADER_BYTES 32
+#define FALCON_MAX_BLOCK 1025
+
+typedef enum { FALCON_F64 = 0, FALCON_F32 = 1 } falcon_dtype;
+
+typedef enum {
+    FALCON_OK = 0,
+    FALCON_ERR_INVALID = 1,     /* bad argument (null pointer, dtype, alignment, ...) */
+    FALCON_ERR_CAPACITY = 2,    /* output buffer too small */
+    FALCON_ERR_CORRUPT = 3,     /* malformed or truncated compressed stream */
+    FALCON_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    FALCON_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (nothing hangs) */
+    FALCON_ERR_UNSUPPORTED = 6  /* valid format parameter the GPU path does not handle */
+} falcon_status;
+
+/* Library version (FALCON_ABI_VERSION). */
+int falcon_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *falcon_status_string(int status);
+
+/* Worst-case stream size in bytes for n values of `dtype` in chunks of block_size:
+ * 32 + 4*ceil(n/B) + sum over chunks of (2 + z1 + 1 + W/8 + W*cols/8), W = 64 (FP64) or 32,
+ * z1 = W/8 bytes.  Pure host function; returns 0 for invalid arguments. */
+size_t falcon_bound(uint64_t n, int dtype, uint32_t block_size);
+
+/* Parses the 32-byte header of a stream held in HOST memory (len >= 32).
+ * Outputs may be NULL.  FALCON_ERR_CORRUPT if the header is malformed. */
+int falcon_stream_info(const void *h_header, size_t len, uint64_t *n, int *dtype,
+                       uint32_t *block_size, uint64_t *num_chunks);
+
+/* Compresses n values at d_in (FP64 or FP32, device) into d_out (device, out_capacity
+ * bytes) and stores the stream length in *out_bytes (host).  Enqueued on `stream`; the
+ * call synchronises that stream once to read the length and status back.  Uses a
+ * per-(device, stream) workspace cached by the library (freed by falcon_release).
+ * Sec. 3 (Alg. 3) of the paper. */
+int falcon_compress(const void *d_in, uint64_t n, int dtype, uint32_t block_size,
+                    void *d_out, size_t out_capacity, size_t *out_bytes, void *stream);
+
+/* Decompresses the stream at d_in (device, in_bytes) into d_out (device,
+ * out_capacity_bytes) and stores the value count in *n_out (host).  Reads the 32-byte
+ * header back to the host first, then enqueues the kernel and synchronises `stream` once
+ * for the status.  Sec. 4 of the paper. */
+int falcon_decompress(const void *d_in, size_t in_bytes, void *d_out, size_t out_capacity_bytes,
+                      uint64_t *n_out, void *stream);
+
+/* Device workspace (bytes) needed by the asynchronous entry points for a stream of
+ * num_chunks chunks.  Must be 256-byte aligned device memory. */
+size_t falcon_workspace_bytes(uint64_t num_chunks);
+
+/* Asynchronous compression: enqueues a workspace reset and the kernel on `stream` and
+ * returns without synchronising, so it can be captured in a CUDA graph.
+ * d_result (device, 2 x uint64): [0] = stream length in bytes, [1] = falcon_status of the
+ * device-side work (the host return value only covers argument checks and launch).
+ * d_workspace: falcon_workspace_bytes(ceil(n / block_size)) bytes of device memory owned
+ * by the caller; calls that share a workspace must be ordered on one stream. */
+int falcon_compress_async(const void *d_in, uint64_t n, int dtype, uint32_t block_size,
+                          void *d_out, size_t out_capacity, void *d_workspace,
+                          size_t workspace_bytes, uint64_t *d_result, void *stream);
+
+/* Asynchronous decompression.  h_header is a HOST copy of the stream's first 32 bytes
+ * (the caller produced the stream or read it back); it sizes the launch.  d_result:
+ * [0] = number of values, [1] = falcon_status.  Workspace and capture rules as above. */
+int falcon_decompress_async(const void *d_in, size_t in_bytes, const void *h_header,
+                            void *d_out, size_t out_capacity_bytes, void *d_workspace,
+                            size_t workspace_bytes, uint64_t *d_result, void *stream);
+
+/* Frees the workspaces cached by falcon_compress / falcon_decompress on every device. */
+int falcon_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FALCON_H_ */

@@ -1,0 +1,403 @@
+// Device-side building blocks of the Falcon kernels (sm_103a).
+//
+// Work decomposition: one warp per chunk of B <= 1025 values.  Lane l owns the 32
+// consecutive delta columns 32l .. 32l+31 (column c holds z_{c+2}, Eq. 5), so a 32x32
+// bit transpose in registers turns each bit plane into one 32-bit word whose
+// little-endian bytes are row bytes 4l .. 4l+3 of that plane (Sec. 3.3, Fig. 8).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "falcon_internal.h"
+
+#define FALCON_TABLE_QUAL static __constant__ const
+#include "falcon_tables.h"
+
+namespace falcon {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagIncl = 2ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+// Bounded waits: a look-back spin gives up after this many SM clock cycles (~1.5 s).
+constexpr long long kSpinLimit = 3000000000ll;
+
+template <bool F64> struct Traits;
+template <> struct Traits<true> {
+    using U = uint64_t;
+    static constexpr int W = 64;            // bits per value
+    static constexpr int S = 8;             // bytes per value
+    static constexpr int Z1B = 8;           // bytes of z_1 in a record
+    static constexpr int A_MAX = 22;        // Case 1: alpha_max <= 22 (Thm 3)
+    static constexpr int B_MAX = 15;        // Case 1: beta_hat_max <= 15 (Thm 2)
+    static constexpr int A_SENT = 23;       // Case-2 header sentinels
+    static constexpr int B_SENT = 16;
+    static constexpr int UNITS = 16;        // 16-byte units per lane (32 values)
+};
+template <> struct Traits<false> {
+    using U = uint32_t;
+    static constexpr int W = 32;
+    static constexpr int S = 4;
+    static constexpr int Z1B = 4;
+    static constexpr int A_MAX = 10;        // 5^10 < 2^24: 10^alpha exact in FP32
+    static constexpr int B_MAX = 7;         // 10^7 < 2^24
+    static constexpr int A_SENT = 11;
+    static constexpr int B_SENT = 8;
+    static constexpr int UNITS = 8;
+};
+
+// --------------------------------------------------------------------------------------
+// small helpers
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t zigzag(uint64_t x) { return (x << 1) ^ (uint64_t)((int64_t)x >> 63); }
+__device__ __forceinline__ uint32_t zigzag(uint32_t x) { return (x << 1) ^ (uint32_t)((int32_t)x >> 31); }
+__device__ __forceinline__ uint64_t unzigzag(uint64_t z) { return (z >> 1) ^ (0ull - (z & 1ull)); }
+__device__ __forceinline__ uint32_t unzigzag(uint32_t z) { return (z >> 1) ^ (0u - (z & 1u)); }
+
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
+    return ((uint64_t)__shfl_sync(kFull, (uint32_t)(v >> 32), src) << 32) |
+           __shfl_sync(kFull, (uint32_t)v, src);
+}
+__device__ __forceinline__ uint64_t shfl_down_u64(uint64_t v, int d) {
+    return ((uint64_t)__shfl_down_sync(kFull, (uint32_t)(v >> 32), d) << 32) |
+           __shfl_down_sync(kFull, (uint32_t)v, d);
+}
+__device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v, int d) {
+    return ((uint64_t)__shfl_up_sync(kFull, (uint32_t)(v >> 32), d) << 32) |
+           __shfl_up_sync(kFull, (uint32_t)v, d);
+}
+__device__ __forceinline__ uint32_t shfl_x(uint32_t v, int src) { return __shfl_sync(kFull, v, src); }
+__device__ __forceinline__ uint64_t shfl_x(uint64_t v, int src) { return shfl_u64(v, src); }
+__device__ __forceinline__ uint32_t shfl_down_x(uint32_t v, int d) { return __shfl_down_sync(kFull, v, d); }
+__device__ __forceinline__ uint64_t shfl_down_x(uint64_t v, int d) { return shfl_down_u64(v, d); }
+__device__ __forceinline__ uint32_t shfl_up_x(uint32_t v, int d) { return __shfl_up_sync(kFull, v, d); }
+__device__ __forceinline__ uint64_t shfl_up_x(uint64_t v, int d) { return shfl_up_u64(v, d); }
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += ((uint64_t)__shfl_xor_sync(kFull, (uint32_t)(v >> 32), o) << 32) |
+                                          __shfl_xor_sync(kFull, (uint32_t)v, o);
+    return v;
+}
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+    uint32_t hi = __reduce_max_sync(kFull, (uint32_t)(v >> 32));
+    uint32_t lo = __reduce_max_sync(kFull, ((uint32_t)(v >> 32) == hi) ? (uint32_t)v : 0u);
+    return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ uint32_t warp_max_x(uint32_t v) { return __reduce_max_sync(kFull, v); }
+__device__ __forceinline__ uint64_t warp_max_x(uint64_t v) { return warp_max_u64(v); }
+__device__ __forceinline__ uint32_t warp_or_x(uint32_t v) { return __reduce_or_sync(kFull, v); }
+__device__ __forceinline__ uint64_t warp_or_x(uint64_t v) {
+    return ((uint64_t)__reduce_or_sync(kFull, (uint32_t)(v >> 32)) << 32) | __reduce_or_sync(kFull, (uint32_t)v);
+}
+// exclusive prefix sum of a 64-bit lane value over the warp
+__device__ __forceinline__ uint64_t warp_exclusive_u64(uint64_t v, int lane) {
+    uint64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint64_t t = shfl_up_u64(incl, o);
+        if (lane >= o) incl += t;
+    }
+    return incl - v;
+}
+
+// number of zero bytes of a 32-bit word (exact)
+__device__ __forceinline__ int zero_bytes(uint32_t x) {
+    uint32_t y = (x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;
+    y = ~(y | x | 0x7F7F7F7Fu);
+    return __popc(y);
+}
+// 4-bit mask, bit (3-i) set iff byte i of x is non-zero
+__device__ __forceinline__ uint32_t nonzero_nibble(uint32_t x) {
+    uint32_t y = (x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;
+    y = (y | x) & 0x80808080u;          // bit 8i+7 set iff byte i != 0
+    return ((y >> 4) & 8u) | ((y >> 13) & 4u) | ((y >> 22) & 2u) | ((y >> 31) & 1u);
+}
+
+// --------------------------------------------------------------------------------------
+// 32x32 bit transpose in registers: afterwards bit j of a[i] = old bit i of a[j].
+// Recursive exchange of the off-diagonal blocks (Hacker's Delight, Sec. 7-3).
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
+#define FALCON_TSTEP(h, mask)                                                       \
+    _Pragma("unroll") for (int k = 0; k < 32; ++k) {                               \
+        if ((k & (h)) == 0) {                                                       \
+            uint32_t t = ((a[k] >> (h)) ^ a[k + (h)]) & (mask);                     \
+            a[k + (h)] ^= t;                                                        \
+            a[k] ^= t << (h);                                                       \
+        }                                                                           \
+    }
+    FALCON_TSTEP(16, 0x0000FFFFu)
+    FALCON_TSTEP(8, 0x00FF00FFu)
+    FALCON_TSTEP(4, 0x0F0F0F0Fu)
+    FALCON_TSTEP(2, 0x33333333u)
+    FALCON_TSTEP(1, 0x55555555u)
+#undef FALCON_TSTEP
+}
+
+// --------------------------------------------------------------------------------------
+// Shared-memory staging of a chunk's values, swizzled so that lane l's 16-byte units
+// (values 32l .. 32l+31) are read conflict-free: unit u of lane L sits at L*UNITS + (u^(L&7)).
+// --------------------------------------------------------------------------------------
+template <bool F64>
+__device__ __forceinline__ uint32_t phys_unit(uint32_t q) {
+    constexpr int UN = Traits<F64>::UNITS;
+    uint32_t L = q / UN, u = q % UN;
+    return L * UN + (u ^ (L & 7u));
+}
+template <bool F64>
+__device__ __forceinline__ uint32_t phys_elem_byte(uint32_t e) {
+    constexpr int S = Traits<F64>::S;
+    constexpr int PER = 16 / S;       // values per unit
+    return phys_unit<F64>(e / PER) * 16u + (e % PER) * S;
+}
+
+// Loads m values (m <= 1025) from global src into the warp's staging buffer.
+template <bool F64>
+__device__ __forceinline__ void stage_values(const uint8_t *src, uint32_t m, uint8_t *wsm, int lane) {
+    constexpr int S = Traits<F64>::S;
+    const uint32_t base = smem_addr(wsm);
+    const uint32_t nbytes = m * S;
+    uint32_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        const uint32_t nunits = nbytes >> 4;
+        for (uint32_t q = lane; q < nunits; q += 32) cp_async16(base + phys_unit<F64>(q) * 16u, src + 16u * q);
+        done = (nunits * 16u) / S;
+    }
+    for (uint32_t e = done + lane; e < m; e += 32) {
+        if constexpr (F64) cp_async8(base + phys_elem_byte<F64>(e), src + (size_t)e * S);
+        else cp_async4(base + phys_elem_byte<F64>(e), src + (size_t)e * S);
+    }
+    cp_async_wait_all();
+    __syncwarp();
+}
+
+// Lane reads its 32 values (indices 32*lane + k); indices >= m read as +0.
+template <bool F64>
+__device__ __forceinline__ void read_own(const uint8_t *wsm, int lane, uint32_t m,
+                                         typename Traits<F64>::U (&v)[32]) {
+    using U = typename Traits<F64>::U;
+    constexpr int UN = Traits<F64>::UNITS;
+    constexpr int PER = 32 / UN;
+#pragma unroll
+    for (int u = 0; u < UN; ++u) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(wsm + (lane * UN + (u ^ (lane & 7))) * 16);
+        if constexpr (F64) {
+            v[PER * u + 0] = ((U)q.y << 32) | q.x;
+            v[PER * u + 1] = ((U)q.w << 32) | q.z;
+        } else {
+            v[PER * u + 0] = q.x;
+            v[PER * u + 1] = q.y;
+            v[PER * u + 2] = q.z;
+            v[PER * u + 3] = q.w;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+        if ((uint32_t)(32 * lane + k) >= m) v[k] = 0;
+}
+
+template <bool F64>
+__device__ __forceinline__ typename Traits<F64>::U read_elem(const uint8_t *wsm, uint32_t e) {
+    using U = typename Traits<F64>::U;
+    return *reinterpret_cast<const U *>(wsm + phys_elem_byte<F64>(e));
+}
+
+// --------------------------------------------------------------------------------------
+// Classification (R1: -0, NaN, inf, subnormals are exceptions)
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ bool is_special(uint64_t u) {
+    const uint64_t a = u & 0x7FFFFFFFFFFFFFFFull;
+    return (u != 0) && (a - 0x0010000000000000ull >= 0x7FE0000000000000ull);
+}
+__device__ __forceinline__ bool is_special(uint32_t u) {
+    const uint32_t a = u & 0x7FFFFFFFu;
+    return (u != 0) && (a - 0x00800000u >= 0x7F000000u);
+}
+
+// floor(log10 a) as the largest k with a >= fl(10^k), for a normal, positive, with binary
+// exponent in the table's reach (checked by the caller).
+__device__ __forceinline__ int floor_log10(uint64_t a) {
+    const int e2 = (int)(a >> 52) - 1023;
+    int k = (e2 * 78913) >> 18;        // floor(e2 * log10 2) up to +-1
+    if (a >= FALCON_P10_F64[k + 1 - FALCON_P10_F64_LO]) ++k;
+    else if (a < FALCON_P10_F64[k - FALCON_P10_F64_LO]) --k;
+    return k;
+}
+__device__ __forceinline__ int floor_log10(uint32_t a) {
+    const int e2 = (int)(a >> 23) - 127;
+    int k = (e2 * 78913) >> 18;
+    if (a >= FALCON_P10_F32[k + 1 - FALCON_P10_F32_LO]) ++k;
+    else if (a < FALCON_P10_F32[k - FALCON_P10_F32_LO]) --k;
+    return k;
+}
+// binary-exponent window where floor_log10 is defined and Case 1 is reachable
+__device__ __forceinline__ bool log10_in_range(uint64_t a) {
+    const uint32_t be = (uint32_t)(a >> 52);
+    return be >= 1023u - 90u && be < 1023u + 50u;
+}
+__device__ __forceinline__ bool log10_in_range(uint32_t a) {
+    const uint32_t be = a >> 23;
+    return be >= 127u - 40u && be < 127u + 24u;
+}
+
+// --------------------------------------------------------------------------------------
+// The per-value test of Alg. 2 at decimal place a, in exact integer arithmetic.
+//
+// Alg. 2 accepts a for v when v (x) 10^a lies within |x| 2^-52 of an integer (eps <= mu)
+// and round(x) / 10^a gives back v.  With v = m 2^E, P = m 5^a and F = -(E + a), the exact
+// product is X = P / 2^F; for |X| < 2^50 both conditions together are equivalent to
+//   fl(N / 10^a) == v   with N = round(X),
+// i.e. |N 2^F - P| < 5^a / 2 (5^a / 4 below a power of two), because the rounding interval
+// of v scaled by 10^a is exactly that wide.  The same holds for FP32 (exact x, R14).
+// Callers only ask for a with |X| < 10^15 (FP32: < 10^7).
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ bool q_test(uint64_t u, int a) {
+    const uint64_t au = u & 0x7FFFFFFFFFFFFFFFull;
+    if (au == 0) return true;
+    const int E = (int)(au >> 52) - 1075;
+    const uint64_t m = (au & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int F = -(E + a);
+    if (F <= 0) return true;
+    if (F >= 128) return false;
+    const uint64_t p5 = FALCON_POW5[a];
+    const unsigned __int128 P = (unsigned __int128)m * p5;
+    const unsigned __int128 one = 1;
+    const unsigned __int128 r = P & ((one << F) - 1);
+    const unsigned __int128 half = one << (F - 1);
+    const uint64_t lim = p5 >> 1;
+    if (r >= half) return ((one << F) - r) <= lim;
+    return r <= ((m == 0x0010000000000000ull) ? ((p5 - 1) >> 2) : lim);
+}
+__device__ __forceinline__ bool q_test(uint32_t u, int a) {
+    const uint32_t au = u & 0x7FFFFFFFu;
+    if (au == 0) return true;
+    const int E = (int)(au >> 23) - 150;
+    const uint64_t m = (au & 0x007FFFFFu) | 0x00800000u;
+    const int F = -(E + a);
+    if (F <= 0) return true;
+    if (F >= 64) return false;
+    const uint64_t p5 = FALCON_POW5[a];
+    const uint64_t P = m * p5;
+    const uint64_t r = P & ((1ull << F) - 1);
+    const uint64_t half = 1ull << (F - 1);
+    const uint64_t lim = p5 >> 1;
+    if (r >= half) return ((1ull << F) - r) <= lim;
+    return r <= ((m == 0x00800000u) ? ((p5 - 1) >> 2) : lim);
+}
+
+// g = round(v (x) 10^a) (Eq. 4, Case 1) for a value that passed q_test at a.
+__device__ __forceinline__ uint64_t case1_g(uint64_t u, int a) {
+    const uint64_t au = u & 0x7FFFFFFFFFFFFFFFull;
+    if (au == 0) return 0;
+    const int E = (int)(au >> 52) - 1075;
+    const uint64_t m = (au & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const int F = -(E + a);
+    const uint64_t p5 = FALCON_POW5[a];
+    const unsigned __int128 P = (unsigned __int128)m * p5;
+    uint64_t N;
+    if (F <= 0) N = (uint64_t)(P << (-F));
+    else N = (uint64_t)((P + ((unsigned __int128)1 << (F - 1))) >> F);
+    return (u >> 63) ? (0ull - N) : N;
+}
+__device__ __forceinline__ uint32_t case1_g(uint32_t u, int a) {
+    const uint32_t au = u & 0x7FFFFFFFu;
+    if (au == 0) return 0;
+    const int E = (int)(au >> 23) - 150;
+    const uint64_t m = (au & 0x007FFFFFu) | 0x00800000u;
+    const int F = -(E + a);
+    const uint64_t P = m * FALCON_POW5[a];
+    uint64_t N;
+    if (F <= 0) N = P << (-F);
+    else N = (P + (1ull << (F - 1))) >> F;
+    return (u >> 31) ? (0u - (uint32_t)N) : (uint32_t)N;
+}
+
+// --------------------------------------------------------------------------------------
+// Decoupled look-back over the chunks of one job (Sec. 3.4): publishes this chunk's
+// aggregate, sums predecessors until an inclusive prefix is found, publishes its own
+// inclusive prefix and returns the exclusive prefix.  Every wait is bounded: on timeout
+// (or when another warp already gave up) it sets ctl->abort and returns ok = false.
+// --------------------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t lookback(unsigned long long *flags, uint64_t c, uint64_t agg,
+                                             int lane, Control *ctl, bool &ok) {
+    ok = true;
+    if (c == 0) {
+        if (lane == 0) st_relaxed(&flags[0], kFlagIncl | agg);
+        return 0;
+    }
+    if (lane == 0) st_relaxed(&flags[c], kFlagAgg | agg);
+    uint64_t excl = 0;
+    int64_t top = (int64_t)c - 1;
+    const long long t0 = clock64();
+    while (true) {
+        const int64_t idx = top - lane;
+        const unsigned long long f = (idx >= 0) ? ld_relaxed(&flags[idx]) : kFlagIncl;
+        const uint32_t st = (uint32_t)(f >> 62);
+        const unsigned incl_mask = __ballot_sync(kFull, st == 2u);
+        const unsigned notready = __ballot_sync(kFull, st == 0u);
+        const int p = incl_mask ? __ffs(incl_mask) - 1 : 32;
+        const unsigned need = (p >= 31) ? kFull : ((2u << p) - 1u);
+        if (notready & need) {
+            bool give_up = false;
+            if (lane == 0)
+                give_up = (clock64() - t0 > kSpinLimit) ||
+                          (*reinterpret_cast<volatile unsigned int *>(&ctl->abort) != 0);
+            if (__shfl_sync(kFull, give_up ? 1 : 0, 0)) {
+                if (lane == 0) atomicExch(&ctl->abort, 1u);
+                ok = false;
+                return 0;
+            }
+            continue;
+        }
+        const uint64_t val = (lane <= p) ? (f & kValMask) : 0ull;
+        excl += warp_sum_u64(val);
+        if (p < 32) break;
+        top -= 32;
+    }
+    if (lane == 0) st_relaxed(&flags[c], kFlagIncl | (excl + agg));
+    return excl;
+}
+
+__device__ __forceinline__ void set_status(unsigned long long *result, uint32_t code) {
+    atomicCAS(&result[1], 0ull, (unsigned long long)code);
+}
+
+// Finds the job that owns global ticket t (jobs sorted by chunk_begin).
+__device__ __forceinline__ int find_job(const Job *jobs, int njobs, uint64_t t) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].chunk_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t chunk_cols(uint32_t m) { return m <= 1 ? 0u : ((m - 1u + 63u) & ~63u); }
+
+}  // namespace falcon

@@ -1,0 +1,56 @@
+// Host/device shared declarations of libfalcon (not part of the public ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace falcon {
+
+constexpr int kWarpsPerCta = 4;
+constexpr int kThreads = 32 * kWarpsPerCta;
+constexpr uint32_t kMaxBlock = 1025;
+// Shared memory per warp: the staged chunk (<= 1025 * 8 bytes + one extra 16-byte unit)
+// and, later, the compressed record (<= 8211 bytes) at a 0..15 byte shift, + 4 spare.
+constexpr int kWarpSmem = 8256;
+constexpr int kCtaSmem = kWarpSmem * kWarpsPerCta;
+
+// Status codes (identical numbering to falcon_status in include/falcon.h).
+enum : uint32_t { kOk = 0, kErrInvalid = 1, kErrCapacity = 2, kErrCorrupt = 3, kErrCuda = 4,
+                  kErrTimeout = 5, kErrUnsupported = 6 };
+
+// One series to compress or decompress.
+//   compress:   in = values (n * S bytes), out = stream (out_cap bytes)
+//   decompress: in = stream (in_bytes),    out = values (out_cap bytes)
+struct Job {
+    const uint8_t *in;
+    uint8_t *out;
+    uint64_t in_bytes;
+    uint64_t out_cap;
+    uint64_t n;
+    uint64_t nchunks;
+    uint64_t chunk_begin;          // first global work ticket of this job
+    unsigned long long *flags;     // nchunks decoupled look-back words
+    unsigned long long *result;    // [0] stream bytes (compress) / values (decompress), [1] status
+    uint32_t block;
+    uint32_t dtype;                // 0 = FP64, 1 = FP32
+};
+
+// Per-launch control block at the start of the workspace (zeroed before each launch).
+struct Control {
+    unsigned long long ticket;     // next work item
+    unsigned int abort;            // set when a bounded wait gives up; everyone bails out
+    unsigned int pad[13];
+};
+static_assert(sizeof(Control) == 64, "control block is 64 bytes");
+
+constexpr size_t kControlBytes = 256;   // control block region (keeps flags 256-aligned)
+
+cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single,
+                            uint64_t total_chunks, Control *ctl, cudaStream_t stream);
+cudaError_t launch_decompress(const Job *d_jobs, int njobs, const Job &single,
+                              uint64_t total_chunks, Control *ctl, cudaStream_t stream);
+
+// Grid size used for a launch over total_chunks work items (persistent, occupancy-bound).
+int compress_grid(uint64_t total_chunks);
+int decompress_grid(uint64_t total_chunks);
+
+}  // namespace falcon

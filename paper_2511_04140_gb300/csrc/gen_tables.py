@@ -1,0 +1,54 @@
+"""Writes falcon_tables.h: the constants the CUDA kernels need, computed from exact
+rational arithmetic (Python's Fraction -> float conversion rounds exactly once).
+
+  FALCON_POW5[a]          5^a for a = 0..22 (exact integers)
+  FALCON_P10_F64[k - LO]  bits of fl64(10^k), k in [-30, 22]
+  FALCON_P10_F32[k - LO]  bits of fl32(10^k), k in [-15, 10]
+
+Run: python gen_tables.py > falcon_tables.h
+"""
+import struct
+from fractions import Fraction
+
+F64_LO, F64_HI = -30, 22
+F32_LO, F32_HI = -15, 10
+
+
+def f64_bits(q: Fraction) -> int:
+    return struct.unpack("<Q", struct.pack("<d", float(q)))[0]
+
+
+def f32_nearest_bits(q: Fraction) -> int:
+    """Bits of the FP32 value nearest to q (ties to even), found without double rounding."""
+    d = float(q)
+    b = struct.unpack("<I", struct.pack("<f", d))[0]
+    best = None
+    for cand in (b - 1, b, b + 1):
+        val = Fraction(struct.unpack("<f", struct.pack("<I", cand))[0])
+        err = abs(val - q)
+        key = (err, cand & 1)
+        if best is None or key < best[0]:
+            best = (key, cand)
+    return best[1]
+
+
+def main():
+    out = ["/* Generated by gen_tables.py -- exact constants for the Falcon kernels. */",
+           "#pragma once", "#include <stdint.h>", "",
+           "#ifndef FALCON_TABLE_QUAL", "#define FALCON_TABLE_QUAL static const", "#endif", "",
+           f"#define FALCON_P10_F64_LO ({F64_LO})", f"#define FALCON_P10_F64_HI ({F64_HI})",
+           f"#define FALCON_P10_F32_LO ({F32_LO})", f"#define FALCON_P10_F32_HI ({F32_HI})", "",
+           "FALCON_TABLE_QUAL uint64_t FALCON_POW5[23] = {"]
+    out += [f"    0x{5 ** a:016x}ull, /* 5^{a} */" for a in range(23)]
+    out += ["};", "", f"FALCON_TABLE_QUAL uint64_t FALCON_P10_F64[{F64_HI - F64_LO + 1}] = {{"]
+    out += [f"    0x{f64_bits(Fraction(10) ** k):016x}ull, /* fl64(1e{k}) */"
+            for k in range(F64_LO, F64_HI + 1)]
+    out += ["};", "", f"FALCON_TABLE_QUAL uint32_t FALCON_P10_F32[{F32_HI - F32_LO + 1}] = {{"]
+    out += [f"    0x{f32_nearest_bits(Fraction(10) ** k):08x}u, /* fl32(1e{k}) */"
+            for k in range(F32_LO, F32_HI + 1)]
+    out += ["};", ""]
+    print("\n".join(out))
+
+
+if __name__ == "__main__":
+    main()
