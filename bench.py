@@ -1,0 +1,343 @@
+#!/usr/bin/env python3
+"""Throughput bench of libfalcon on the 67,108,864-value segment workload.
+
+One step = compress + decompress of the FP64 array and of the FP32 array (four kernel
+launches), inputs resident in HBM.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl falcon|reference]
+
+Under torchrun each rank runs its own replica on its own GPU (chunks are independent:
+weak scaling, no collective on the data path); value = bytes of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_VALUES = 1 << 26
+BLOCK = 1024
+METRIC = "comp/decomp GB/s & % HBM peak, bit-exact; batched vs plain; serve p99 ms"
+WORKLOAD = ("segments: 67,108,864 values, once FP64 and once FP32; 4096-value segments with "
+            "0..6 decimal places, sinusoid amplitude 10^U(0,4) + AR(1) noise, 1% full-precision "
+            "outliers, 0.01% NaN/inf/subnormal/-0; block 1024")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="falcon", choices=["falcon", "reference"])
+    ap.add_argument("--n", type=int, default=N_VALUES, help=argparse.SUPPRESS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The CPU oracle (the method's plain definition) timed on the host, on a bounded sample
+    of the same workload; rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle
+    from paper_2511_04140_gb300 import synth
+    oracle.build()
+    sample = 1 << 18
+    a64 = synth.segments(args.n, seed=1)[:sample].copy()
+    a32 = synth.segments(args.n, seed=1, dtype=np.float32)[:sample].copy()
+    orig = a64.nbytes + a32.nbytes
+
+    def step():
+        for a in (a64, a32):
+            s = oracle.compress(a, BLOCK)
+            oracle.decompress(s)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t0) / args.steps
+    gbs = 2 * orig / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64/int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": args.n, "block": BLOCK, "sample_values_per_dtype": sample},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {sample} values of the FP64 and of the FP32 array, "
+                                       "compress + decompress, single thread"},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(n):
+    from oracle import oracle
+    from paper_2511_04140_gb300 import synth
+    oracle.build()
+    sample = 1 << 20
+    a64 = synth.segments(n, seed=1)[:sample].copy()
+    a32 = synth.segments(n, seed=1, dtype=np.float32)[:sample].copy()
+    t0 = time.perf_counter()
+    for a in (a64, a32):
+        s = oracle.compress(a, BLOCK)
+        oracle.decompress(s)
+    dt = time.perf_counter() - t0
+    return {"value": 2 * (a64.nbytes + a32.nbytes) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {sample} values of the FP64 and of the FP32 array (1/64 of the workload), "
+                      f"compress + decompress, single thread, {dt:.1f} s"}
+
+
+# ------------------------------------------------------------------------------ falcon arm
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_2511_04140_gb300 import build as fbuild
+    fbuild.build()
+    from paper_2511_04140_gb300 import falcon, synth
+
+    n = args.n
+    host = {np.float64: synth.segments(n, seed=1), np.float32: synth.segments(n, seed=1, dtype=np.float32)}
+    stream = torch.cuda.Stream(device=dev)
+    st_ptr = stream
+    bufs = {}
+    for dt, arr in host.items():
+        code = falcon.F64 if dt == np.float64 else falcon.F32
+        x = torch.from_numpy(arr).to(dev)
+        nc = (n + BLOCK - 1) // BLOCK
+        cap = falcon.bound(n, code, BLOCK)
+        bufs[dt] = dict(x=x, code=code, out=torch.empty(cap, dtype=torch.uint8, device=dev),
+                        y=torch.empty_like(x),
+                        ws_c=torch.zeros(falcon.workspace_bytes(nc), dtype=torch.uint8, device=dev),
+                        ws_d=torch.zeros(falcon.workspace_bytes(nc), dtype=torch.uint8, device=dev),
+                        res_c=torch.zeros(2, dtype=torch.int64, device=dev),
+                        res_d=torch.zeros(2, dtype=torch.int64, device=dev))
+    # stream lengths (needed by the async decompress) from one untimed call
+    for dt, b in bufs.items():
+        s = falcon.compress(b["x"], BLOCK, out=b["out"])
+        b["nbytes"] = s.numel()
+        b["header"] = s[:32].cpu().numpy().tobytes()
+    torch.cuda.synchronize(dev)
+
+    kernels = [("compress_f64", np.float64, "c"), ("decompress_f64", np.float64, "d"),
+               ("compress_f32", np.float32, "c"), ("decompress_f32", np.float32, "d")]
+
+    def step(events=None):
+        for i, (name, dt, kind) in enumerate(kernels):
+            b = bufs[dt]
+            if events is not None:
+                events[i][0].record(stream)
+            if kind == "c":
+                falcon.compress_async(b["x"], BLOCK, b["out"], b["ws_c"], b["res_c"], st_ptr)
+            else:
+                falcon.decompress_async(b["out"], b["nbytes"], b["header"], b["y"], b["ws_d"], b["res_d"], st_ptr)
+            if events is not None:
+                events[i][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in kernels]
+          for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize(dev)
+        with torch.cuda.stream(stream):
+            start.record(stream)
+            for k in range(args.steps):
+                step(ev[k])
+            stop.record(stream)
+        torch.cuda.synchronize(dev)
+    elapsed_ms = start.elapsed_time(stop)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    # results and bit-exactness (outside the timed region)
+    ok = True
+    for dt, b in bufs.items():
+        nb, stc = (int(v) for v in b["res_c"].cpu())
+        nv, std = (int(v) for v in b["res_d"].cpu())
+        u = torch.int64 if dt == np.float64 else torch.int32
+        ok &= (stc == 0 and std == 0 and nb == b["nbytes"] and nv == n and
+               torch.equal(b["y"].view(u), b["x"].view(u)))
+
+    per = {name: [ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)]
+           for i, (name, _, _) in enumerate(kernels)}
+    peak, peak_kind = measured_peaks()
+    orig = {np.float64: n * 8, np.float32: n * 4}
+    kstats = {}
+    for name, dt, kind in kernels:
+        ms = statistics.mean(per[name])
+        alg = orig[dt] + bufs[dt]["nbytes"]                      # read + write, either direction
+        kstats[name] = {"ms": ms, "gbs_original": orig[dt] / ms / 1e6,
+                        "hbm_gbs": alg / ms / 1e6, "hbm_frac": alg / ms / 1e6 / peak,
+                        "ratio": bufs[dt]["nbytes"] / orig[dt]}
+    dom = max(kstats, key=lambda k: kstats[k]["ms"])
+    ms_per_step = elapsed_ms / args.steps
+    step_bytes = 2 * (orig[np.float64] + orig[np.float32])
+    value = step_bytes * world / (ms_per_step / 1e3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64/int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "block": BLOCK, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (512 MiB FP64 + 256 MiB FP32)"},
+        "bit_exact": bool(ok),
+        "gpu_launches": len(kernels) * args.steps,
+        "kernels": kstats,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": kstats[dom]["hbm_gbs"], "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": kstats[dom]["hbm_frac"],
+                     "traffic": None},
+        "clocks": clocks.summary(),
+    }
+    if rank == 0 and not args.no_e2e:
+        line["e2e"] = e2e(falcon, torch, bufs, host, dev, args)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(n)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e(falcon, torch, bufs, host, dev, args):
+    """Same metric through the public API with host buffers: pinned H2D of the values,
+    compress, D2H of the stream, H2D of the stream, decompress, D2H of the values."""
+    pinned = {}
+    for dt, arr in host.items():
+        b = bufs[dt]
+        pinned[dt] = dict(x=torch.from_numpy(arr).pin_memory(),
+                          s=torch.empty(b["out"].numel(), dtype=torch.uint8).pin_memory(),
+                          y=torch.empty(len(arr), dtype=b["x"].dtype).pin_memory())
+    stream = torch.cuda.current_stream(dev)
+
+    def one():
+        h2d = d2h = 0
+        for dt, p in pinned.items():
+            b = bufs[dt]
+            b["x"].copy_(p["x"], non_blocking=True)
+            h2d += p["x"].numel() * p["x"].element_size()
+            s = falcon.compress(b["x"], BLOCK, out=b["out"])
+            nb = s.numel()
+            p["s"][:nb].copy_(s, non_blocking=True)
+            d2h += nb
+            b["out"][:nb].copy_(p["s"][:nb], non_blocking=True)
+            h2d += nb
+            y = falcon.decompress(b["out"][:nb], out=b["y"])
+            p["y"].copy_(y, non_blocking=True)
+            d2h += p["y"].numel() * p["y"].element_size()
+        return h2d, d2h
+
+    one()
+    torch.cuda.synchronize(dev)
+    reps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        h2d, d2h = one()
+    torch.cuda.synchronize(dev)
+    dt = (time.perf_counter() - t0) / reps
+    orig = sum(a.nbytes for a in host.values())
+    return {"value": 2 * orig / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "mode": "sequential H2D -> compress -> D2H -> H2D -> decompress -> D2H, pinned host buffers"}
+
+
+if __name__ == "__main__":
+    main()

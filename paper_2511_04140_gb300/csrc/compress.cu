@@ -116,6 +116,30 @@ __device__ __forceinline__ int search_alpha(const typename Traits<F64>::U (&v)[3
     return hi;
 }
 
+// FP32: alpha_max = max over values of Alg. 2's decimal place (first_pass_f32), then the
+// R6 check that every value round-trips at alpha_max; -1 means Case 2.
+__device__ __forceinline__ int alpha_f32(const uint32_t (&v)[32], uint32_t vx, uint32_t vmax, int atop) {
+    // quick rejection on the largest magnitude(s)
+    bool fail = ((vx & 0x7FFFFFFFu) == vmax) && first_pass_f32(vx, atop) < 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) fail |= ((v[k] & 0x7FFFFFFFu) == vmax) && first_pass_f32(v[k], atop) < 0;
+    if (__any_sync(kFull, fail)) return -1;
+    int amax = first_pass_f32(vx, atop);
+    bool bad = amax < 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const int a = first_pass_f32(v[k], atop);
+        bad |= a < 0;
+        amax = a > amax ? a : amax;
+    }
+    if (__any_sync(kFull, bad)) return -1;
+    amax = (int)__reduce_max_sync(kFull, (uint32_t)amax);
+    bool rt = q_test(vx, amax);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) rt &= q_test(v[k], amax);
+    return __all_sync(kFull, rt) ? amax : -1;
+}
+
 template <bool F64>
 __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *wsm, int lane, int &hint,
                                Control *ctl) {
@@ -157,14 +181,16 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *wsm, int lan
             const int e_max = floor_log10(vmax);
             const int atop = min(T::A_MAX, T::B_MAX - 1 - e_max);
             if (atop >= 0) {
-                // quick rejection: test the largest magnitude(s) first
-                bool fail = ((vx & ABS) == vmax) && !q_test(vx, atop);
+                if constexpr (F64) {
+                    // quick rejection: test the largest magnitude(s) first
+                    bool fail = ((vx & ABS) == vmax) && !q_test(vx, atop);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) fail |= ((v[k] & ABS) == vmax) && !q_test(v[k], atop);
-                if (!__any_sync(kFull, fail)) {
-                    alpha = search_alpha<F64>(v, vx, atop, hint);
-                    if (alpha >= 0) beta_hat = alpha + e_max + 1;
+                    for (int k = 0; k < 32; ++k) fail |= ((v[k] & ABS) == vmax) && !q_test(v[k], atop);
+                    if (!__any_sync(kFull, fail)) alpha = search_alpha<F64>(v, vx, atop, hint);
+                } else {
+                    alpha = alpha_f32(v, vx, vmax, atop);
                 }
+                if (alpha >= 0) beta_hat = alpha + e_max + 1;
             }
         }
     }

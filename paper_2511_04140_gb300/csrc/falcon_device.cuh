@@ -310,6 +310,35 @@ __device__ __forceinline__ bool q_test(uint32_t u, int a) {
     return r <= ((m == 0x00800000u) ? ((p5 - 1) >> 2) : lim);
 }
 
+// Alg. 2's first test alone (eps <= mu) for FP32, on the exact product x = v * 10^a (R14):
+// the distance of X = P / 2^F to the nearest integer is at most X * 2^-23.
+__device__ __forceinline__ bool eps_le_mu(uint32_t u, int a) {
+    const uint32_t au = u & 0x7FFFFFFFu;
+    if (au == 0) return true;
+    const int E = (int)(au >> 23) - 150;
+    const uint64_t m = (au & 0x007FFFFFu) | 0x00800000u;
+    const int F = -(E + a);
+    if (F <= 0) return true;
+    if (F >= 64) return false;
+    const uint64_t P = m * FALCON_POW5[a];
+    const uint64_t r = P & ((1ull << F) - 1);
+    const uint64_t rc = (1ull << F) - r;
+    const uint64_t dist = r < rc ? r : rc;
+    return dist <= (P >> 23);
+}
+
+// FP32 decimal place of one value as Alg. 2 finds it, restricted to [0, atop]: the first a
+// with eps <= mu, accepted only if the round trip holds there; -1 otherwise (an exception
+// or a decimal place beyond atop, both of which make the chunk Case 2).  The 24-bit
+// significand leaves no margin for Thm 4 at beta = 7, so early spurious passes are real
+// and must be reproduced value by value.
+__device__ __forceinline__ int first_pass_f32(uint32_t u, int atop) {
+    if ((u & 0x7FFFFFFFu) == 0) return 0;
+    for (int a = 0; a <= atop; ++a)
+        if (eps_le_mu(u, a)) return q_test(u, a) ? a : -1;
+    return -1;
+}
+
 // g = round(v (x) 10^a) (Eq. 4, Case 1) for a value that passed q_test at a.
 __device__ __forceinline__ uint64_t case1_g(uint64_t u, int a) {
     const uint64_t au = u & 0x7FFFFFFFFFFFFFFFull;

@@ -159,3 +159,13 @@ def test_delta_is_modular(oracle):
     for i in range(1, len(g)):
         back.append((back[-1] + oracle.unzigzag64(int(z[i]))) % 2 ** 64)
     assert back == [int(x) for x in g]
+
+
+def test_alg2_f32_spurious_early_pass(oracle):
+    """With 24-bit significands the error bound of Thm 4 has no margin at beta = 7:
+    fl32(0.001) - 1 ulp = 0.00099999993 passes eps <= mu already at alpha = 3 (x rounds
+    to 1), the round trip 1/10^3 then fails, so Alg. 2 reports an exception."""
+    v = np.nextafter(np.float32(0.001), np.float32(-1))
+    assert oracle.dp_ds(v, np.float32) == (11, 8)
+    a, b, case1, _ = oracle.chunk_transform(np.array([v], dtype=np.float32))
+    assert not case1
