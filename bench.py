@@ -36,7 +36,7 @@ WORKLOAD = ("segments: 67,108,864 values, once FP64 and once FP32; 4096-value se
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="falcon", choices=["falcon", "reference"])
     ap.add_argument("--n", type=int, default=N_VALUES, help=argparse.SUPPRESS)
@@ -67,6 +67,12 @@ class ClockSampler:
         self.lines = []
 
     def __enter__(self):
+        self.start()
+        return self
+
+    def start(self):
+        if self.proc is not None:
+            return
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
@@ -74,9 +80,12 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.time()                     # let nvidia-smi come up before timing
+            while not self.lines and time.time() - t0 < 5:
+                time.sleep(0.05)
+            self.lines.clear()
         except Exception:
             self.proc = None
-        return self
 
     def _read(self):
         for line in self.proc.stdout:
@@ -224,6 +233,8 @@ def main():
             if events is not None:
                 events[i][1].record(stream)
 
+    clocks = ClockSampler(local)
+    clocks.start()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
@@ -234,7 +245,8 @@ def main():
     ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in kernels]
           for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clocks:
+    clocks.lines.clear()
+    with clocks:
         torch.cuda.synchronize(dev)
         with torch.cuda.stream(stream):
             start.record(stream)

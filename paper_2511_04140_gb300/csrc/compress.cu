@@ -1,51 +1,54 @@
 // Falcon compression kernel (Sec. 3 of the paper; Alg. 3 CmpKernel) for sm_103a.
 //
-// One persistent launch; each warp repeatedly claims a chunk (dynamic ticket, so that
-// the decoupled look-back only ever waits on chunks already owned by running warps) and
-//   1. stages the chunk's values in shared memory with cp.async (swizzled),
-//   2. decides Case 1 / Case 2 of Eq. 4: specials (R1) and the chunk maximum first, then
-//      the smallest decimal place alpha_max at which every value passes Alg. 2's test
-//      (exact integer arithmetic, see q_test), searched from the warp's previous alpha,
-//   3. computes G (Eq. 4) and Z (Eq. 5), the bit width w and the bit planes (32x32
-//      register transposes),
-//   4. counts the zero bytes of every row (lambda) and picks sparse/dense storage
-//      (Sec. 3.3), which gives the record size,
-//   5. obtains its output offset by decoupled look-back (Sec. 3.4),
-//   6. assembles the record in shared memory at the output's 16-byte phase and writes it
-//      with aligned 16-byte stores.
+// One persistent launch; each warp repeatedly claims a chunk (dynamic ticket, so that the
+// decoupled look-back only waits on chunks owned by running warps).  While it works on one
+// chunk, the next chunk's values are already streaming into its second shared-memory buffer
+// (cp.async, swizzled).  Per chunk:
+//   1. read the lane's 32 values, classify (R1 specials) and take the chunk maximum,
+//   2. Case 1 / Case 2 of Eq. 4: the smallest decimal place alpha_max at which every value
+//      passes Alg. 2's test, in exact integer arithmetic (q_test); FP32 follows Alg. 2 value
+//      by value,
+//   3. G (Eq. 4), Z (Eq. 5) and the bit width w in registers,
+//   4. 32x32 register transposes give one 32-bit word per bit plane (4 row bytes per lane);
+//      the words go to shared memory and their non-zero bytes are counted (Sec. 3.3 lambda),
+//   5. sparse/dense per row -> record size -> decoupled look-back (Sec. 3.4) -> offset,
+//   6. the record is assembled in shared memory at the output's 16-byte phase, in place of
+//      the plane words it consumes, and written with aligned 16-byte stores.
 #include "falcon_device.cuh"
 
 namespace falcon {
 
 namespace {
 
+constexpr int kBuf = 8256;                  // one chunk of values / one record
+constexpr int kScratch = 128;
+constexpr int kWarpBytes = 2 * kBuf + kScratch;
+constexpr int kPlOff = 48;                  // plane words: kPlOff + (W-1-p)*128 + 4*lane
+
 // Byte-stream writer over a warp's shared-memory record buffer.  Bytes before `pos` are
 // final in shared memory except the partial 32-bit word at (sh + pos) & ~3, whose valid
 // low bytes are kept, top-aligned, in `pend` (identical in every lane).
 struct RecordWriter {
-    uint8_t *buf;       // warp buffer (16-byte aligned); the record starts at buf + sh
-    uint32_t sh;        // 0..15
-    uint32_t pos;       // bytes of the record written so far
+    uint8_t *buf;
+    uint32_t sh;
+    uint32_t pos;
     uint32_t pend;
 
-    __device__ __forceinline__ uint32_t abs_pos() const { return sh + pos; }
-
-    __device__ __forceinline__ void reload(int lane) {
-        (void)lane;
+    __device__ __forceinline__ void reload() {
         __syncwarp();
-        const uint32_t P = abs_pos();
+        const uint32_t P = sh + pos;
         const uint32_t s = P & 3u;
         pend = s ? (*reinterpret_cast<const uint32_t *>(buf + (P - s)) << (32u - 8u * s)) : 0u;
     }
     __device__ __forceinline__ void flush(int lane) {
-        const uint32_t P = abs_pos();
+        const uint32_t P = sh + pos;
         const uint32_t s = P & 3u;
         if (lane == 0 && s) *reinterpret_cast<uint32_t *>(buf + (P - s)) = pend >> (32u - 8u * s);
         __syncwarp();
     }
-    // A dense row: lane l < nact holds row bytes 4l .. 4l+3 in x (little-endian).
+    // dense row: lane l < nact holds row bytes 4l .. 4l+3 (little-endian) in x
     __device__ __forceinline__ void dense(uint32_t x, int lane, uint32_t nact) {
-        const uint32_t P = abs_pos();
+        const uint32_t P = sh + pos;
         const uint32_t s = P & 3u;
         uint32_t prev = __shfl_up_sync(kFull, x, 1);
         if (lane == 0) prev = pend;
@@ -54,10 +57,10 @@ struct RecordWriter {
         pend = __shfl_sync(kFull, x, (int)nact - 1);
         pos += 4u * nact;
     }
-    // A sparse row: bitmap of nact/2 bytes, then the non-zero bytes in row order.
+    // sparse row: bitmap of nact/2 bytes, then the non-zero bytes in row order
     __device__ __forceinline__ void sparse(uint32_t x, int lane, uint32_t nact) {
         flush(lane);
-        const uint32_t P = abs_pos();
+        const uint32_t P = sh + pos;
         const bool active = (uint32_t)lane < nact;
         const uint32_t nib = active ? nonzero_nibble(x) : 0u;
         const uint32_t nib_next = __shfl_down_sync(kFull, nib, 1);
@@ -76,73 +79,90 @@ struct RecordWriter {
             if (active && byte) buf[q++] = (uint8_t)byte;
         }
         pos += nact / 2u + total;
-        reload(lane);
+        reload();
     }
 };
 
+// value k of this lane from the swizzled staging buffer
 template <bool F64>
-__device__ __forceinline__ int search_alpha(const typename Traits<F64>::U (&v)[32],
-                                            typename Traits<F64>::U vx, int atop, int hint) {
-    // smallest a in [0, atop] at which every value passes q_test, or -1 (Case 2).  The
-    // predicate is monotone in a for chunks of valid values (Thm 4 with Thm 3), and a
-    // single failure at atop means some value is an exception or needs alpha > atop.
-    auto all_pass = [&](int a) -> bool {
-        bool ok = q_test(vx, a);
-#pragma unroll
-        for (int k = 0; k < 32; ++k) ok &= q_test(v[k], a);
-        return __all_sync(kFull, ok);
-    };
+__device__ __forceinline__ typename Traits<F64>::U lane_value(const uint8_t *buf, int lane, int k) {
+    using U = typename Traits<F64>::U;
+    constexpr int UN = Traits<F64>::UNITS;
+    constexpr int PER = 16 / Traits<F64>::S;
+    return *reinterpret_cast<const U *>(buf + (lane * UN + ((k / PER) ^ (lane & 7))) * 16 + (k % PER) * Traits<F64>::S);
+}
+
+// Every value of the chunk passes Alg. 2's test at a.  The values are re-read from the
+// staging buffer; this runs a few times per Case-1 chunk only.
+template <bool F64>
+__device__ __noinline__ bool all_pass(const uint8_t *buf, int lane, uint32_t m, typename Traits<F64>::U vx, int a) {
+    bool ok = q_test(vx, a);
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+        if (32u * lane + k < m) ok &= q_test(lane_value<F64>(buf, lane, k), a);
+    }
+    return __all_sync(kFull, ok);
+}
+
+// FP64: smallest a in [0, atop] at which every value passes, or -1 (Case 2).  For chunks of
+// valid values the predicate is monotone in a (Thm 4 with Thm 3); a single failure at atop
+// means some value is an exception or needs alpha > atop.
+__device__ int search_alpha64(const uint8_t *buf, int lane, uint32_t m, uint64_t vx, int atop, int hint) {
     int lo, hi;
     if (hint >= 0 && hint < atop) {
-        if (all_pass(hint)) {
-            if (hint == 0 || !all_pass(hint - 1)) return hint;
+        if (all_pass<true>(buf, lane, m, vx, hint)) {
+            if (hint == 0 || !all_pass<true>(buf, lane, m, vx, hint - 1)) return hint;
             lo = 0;
             hi = hint - 1;
         } else {
-            if (!all_pass(atop)) return -1;
+            if (!all_pass<true>(buf, lane, m, vx, atop)) return -1;
             lo = hint + 1;
             hi = atop;
         }
     } else {
-        if (!all_pass(atop)) return -1;
+        if (!all_pass<true>(buf, lane, m, vx, atop)) return -1;
         lo = 0;
         hi = atop;
     }
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (all_pass(mid)) hi = mid;
+        if (all_pass<true>(buf, lane, m, vx, mid)) hi = mid;
         else lo = mid + 1;
     }
     return hi;
 }
 
-// FP32: alpha_max = max over values of Alg. 2's decimal place (first_pass_f32), then the
-// R6 check that every value round-trips at alpha_max; -1 means Case 2.
-__device__ __forceinline__ int alpha_f32(const uint32_t (&v)[32], uint32_t vx, uint32_t vmax, int atop) {
-    // quick rejection on the largest magnitude(s)
-    bool fail = ((vx & 0x7FFFFFFFu) == vmax) && first_pass_f32(vx, atop) < 0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) fail |= ((v[k] & 0x7FFFFFFFu) == vmax) && first_pass_f32(v[k], atop) < 0;
-    if (__any_sync(kFull, fail)) return -1;
+// FP32: alpha_max = max over values of Alg. 2's decimal place (first_pass_f32), then the R6
+// check that every value round-trips at alpha_max; -1 means Case 2.
+__device__ int alpha32(const uint8_t *buf, int lane, uint32_t m, uint32_t vx, int atop) {
     int amax = first_pass_f32(vx, atop);
     bool bad = amax < 0;
-#pragma unroll
+#pragma unroll 4
     for (int k = 0; k < 32; ++k) {
-        const int a = first_pass_f32(v[k], atop);
-        bad |= a < 0;
-        amax = a > amax ? a : amax;
+        if (32u * lane + k < m) {
+            const int a = first_pass_f32(lane_value<false>(buf, lane, k), atop);
+            bad |= a < 0;
+            amax = a > amax ? a : amax;
+        }
     }
     if (__any_sync(kFull, bad)) return -1;
     amax = (int)__reduce_max_sync(kFull, (uint32_t)amax);
-    bool rt = q_test(vx, amax);
-#pragma unroll
-    for (int k = 0; k < 32; ++k) rt &= q_test(v[k], amax);
-    return __all_sync(kFull, rt) ? amax : -1;
+    return all_pass<false>(buf, lane, m, vx, amax) ? amax : -1;
+}
+
+__device__ __forceinline__ void issue_chunk(const Job *jobs, int njobs, const Job &single, uint64_t t,
+                                            uint8_t *buf, int lane) {
+    const Job &job = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
+    const uint64_t c = t - job.chunk_begin;
+    const uint64_t first = c * (uint64_t)job.block;
+    const uint32_t m = (uint32_t)((job.n - first) < job.block ? (job.n - first) : job.block);
+    if (job.dtype == 0) stage_values_async<true>(job.in + first * 8u, m, buf, lane);
+    else stage_values_async<false>(job.in + first * 4u, m, buf, lane);
 }
 
 template <bool F64>
-__device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *wsm, int lane, int &hint,
-                               Control *ctl) {
+__device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *buf, uint8_t *scratch, int lane,
+                               int &hint, Control *ctl) {
     using T = Traits<F64>;
     using U = typename T::U;
     constexpr U ABS = F64 ? (U)0x7FFFFFFFFFFFFFFFull : (U)0x7FFFFFFFu;
@@ -152,15 +172,11 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *wsm, int lan
     const uint32_t m = (uint32_t)((job.n - first) < B ? (job.n - first) : B);
     const uint64_t data_start = 32ull + 4ull * job.nchunks;
 
-    // ---- 1. stage and read the values ----------------------------------------------
-    stage_values<F64>(job.in + first * T::S, m, wsm, lane);
+    // ---- 1. values, specials, maximum ------------------------------------------------------
     U v[32];
-    read_own<F64>(wsm, lane, m, v);
+    read_own<F64>(buf, lane, m, v);
     U vx = 0;                                   // value 1024 of a 1025-value chunk
-    if (m > 1024u && lane == 31) vx = read_elem<F64>(wsm, 1024);
-    __syncwarp();
-
-    // ---- 2. Case decision (Eq. 4) -----------------------------------------------------
+    if (m > 1024u && lane == 31) vx = read_elem<F64>(buf, 1024);
     bool sp = is_special(vx);
     U vmax = vx & ABS;
 #pragma unroll
@@ -171,6 +187,8 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *wsm, int lan
     }
     sp = __any_sync(kFull, sp);
     vmax = warp_max_x(vmax);
+
+    // ---- 2. Case decision (Eq. 4) -----------------------------------------------------------
     int alpha = -1;                             // -1: Case 2
     int beta_hat = T::B_SENT;
     if (!sp) {
@@ -181,83 +199,128 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *wsm, int lan
             const int e_max = floor_log10(vmax);
             const int atop = min(T::A_MAX, T::B_MAX - 1 - e_max);
             if (atop >= 0) {
-                if constexpr (F64) {
-                    // quick rejection: test the largest magnitude(s) first
-                    bool fail = ((vx & ABS) == vmax) && !q_test(vx, atop);
+                // quick rejection: Alg. 2 on the largest magnitude(s) first
+                bool fail = false;
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) fail |= ((v[k] & ABS) == vmax) && !q_test(v[k], atop);
-                    if (!__any_sync(kFull, fail)) alpha = search_alpha<F64>(v, vx, atop, hint);
-                } else {
-                    alpha = alpha_f32(v, vx, vmax, atop);
+                for (int k = 0; k < 32; ++k) {
+                    if ((v[k] & ABS) == vmax) {
+                        if constexpr (F64) fail |= !q_test(v[k], atop);
+                        else fail |= first_pass_f32(v[k], atop) < 0;
+                    }
                 }
-                if (alpha >= 0) beta_hat = alpha + e_max + 1;
+                if ((vx & ABS) == vmax) {
+                    if constexpr (F64) fail |= !q_test(vx, atop);
+                    else fail |= first_pass_f32(vx, atop) < 0;
+                }
+                if (!__any_sync(kFull, fail)) {
+                    if constexpr (F64) alpha = search_alpha64(buf, lane, m, vx, atop, hint);
+                    else alpha = alpha32(buf, lane, m, vx, atop);
+                }
             }
+            if (alpha >= 0) beta_hat = alpha + e_max + 1;
         }
     }
     hint = alpha;
 
-    // ---- 3. G (Eq. 4) and Z (Eq. 5) ----------------------------------------------------
-    U g[32];
+    // ---- 3. G (Eq. 4) and Z (Eq. 5) ------------------------------------------------------------
     U gx;
     if (alpha >= 0) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) g[k] = case1_g(v[k], alpha);
+        for (int k = 0; k < 32; ++k) v[k] = case1_g(v[k], alpha);
         gx = case1_g(vx, alpha);
     } else {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) g[k] = zigzag(v[k]);
+        for (int k = 0; k < 32; ++k) v[k] = zigzag(v[k]);
         gx = zigzag(vx);
     }
-    const U z1 = shfl_x(g[0], 0);
-    U nxt = shfl_down_x(g[0], 1);
+    const U z1 = shfl_x(v[0], 0);
+    U nxt = shfl_down_x(v[0], 1);
     if (lane == 31) nxt = gx;
-    U z[32];
     U zor = 0;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        const U hi = (k < 31) ? g[k + 1] : nxt;
-        U zz = zigzag((U)(hi - g[k]));
-        if ((uint32_t)(32 * lane + k) + 1u >= m) zz = 0;      // pad columns (R11)
-        z[k] = zz;
-        zor |= zz;
+        const U hi = (k < 31) ? v[k + 1] : nxt;
+        v[k] = zigzag((U)(hi - v[k]));          // v now holds Z of columns 32*lane + k
+        zor |= v[k];
+    }
+    if (32u * lane + 32u >= m) {                 // pad columns (R11): only the last lanes
+        zor = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            if (32u * lane + k + 1u >= m) v[k] = 0;
+            zor |= v[k];
+        }
     }
     zor = warp_or_x(zor);
     const int w = zor ? (T::W - (F64 ? __clzll((long long)zor) : __clz((int)zor))) : 0;
+    __syncwarp();                                // the staging buffer is reused below
 
-    // bit planes: plane word p, bit (k ^ 7) = bit p of z[k]; planes 0..31 in plo,
-    // planes 32..63 (FP64 only) in phi
-    uint32_t plo[32], phi[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        plo[j] = (uint32_t)z[j ^ 7];
-        phi[j] = F64 ? (uint32_t)((uint64_t)z[j ^ 7] >> 32) : 0u;
-    }
-    transpose32(plo);
-    if (F64 && w > 32) transpose32(phi);
-#define FALCON_PLANE(p) ((p) < 32 ? plo[(p) & 31] : phi[(p) & 31])
-
-    // ---- 4. lambda per row, storage choice, record size (Sec. 3.3) --------------------
+    // ---- 4. bit planes -> shared memory, non-zero bytes per row ---------------------------------
     const uint32_t cols = chunk_cols(m);
-    const uint32_t nact = cols / 32u;           // lanes holding row bytes (row = 4*nact bytes)
+    const uint32_t nact = cols / 32u;            // lanes holding row bytes
     const uint32_t row_bytes = cols / 8u;
     const bool active = (uint32_t)lane < nact;
-    uint64_t dense_mask = 0;
-    uint32_t body = 0;
+    uint32_t packed[T::W / 4];
+    {
+        uint32_t a[32];
 #pragma unroll
-    for (int p = 0; p < T::W; ++p) {
-        if (p < w) {
-            const int zc = active ? zero_bytes(FALCON_PLANE(p)) : 0;
-            const uint32_t lam = __reduce_add_sync(kFull, (uint32_t)zc);
-            const bool sparse = lam > cols / 64u;               // tie -> dense (R10)
-            body += sparse ? (cols / 64u + row_bytes - lam) : row_bytes;
-            if (!sparse) dense_mask |= 1ull << p;
+        for (int j = 0; j < 32; ++j) a[j] = (uint32_t)v[j ^ 7];
+        transpose32(a);
+#pragma unroll
+        for (int p = 0; p < 32; ++p) {
+            *reinterpret_cast<uint32_t *>(buf + kPlOff + (T::W - 1 - p) * 128 + 4 * lane) = a[p];
+            const uint32_t nzb = active ? (uint32_t)__popc((((a[p] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | a[p]) & 0x80808080u) : 0u;
+            if (p % 4 == 0) packed[p / 4] = nzb;
+            else packed[p / 4] |= nzb << (8 * (p % 4));
         }
     }
+    if constexpr (F64) {
+        if (w > 32) {
+            uint32_t a[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) a[j] = (uint32_t)((uint64_t)v[j ^ 7] >> 32);
+            transpose32(a);
+#pragma unroll
+            for (int p = 0; p < 32; ++p) {
+                *reinterpret_cast<uint32_t *>(buf + kPlOff + (31 - p) * 128 + 4 * lane) = a[p];
+                const uint32_t nzb = active ? (uint32_t)__popc((((a[p] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | a[p]) & 0x80808080u) : 0u;
+                if (p % 4 == 0) packed[8 + p / 4] = nzb;
+                else packed[8 + p / 4] |= nzb << (8 * (p % 4));
+            }
+        } else {
+#pragma unroll
+            for (int i = 8; i < 16; ++i) packed[i] = 0;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < T::W / 4; ++i) {
+        const uint32_t s = __reduce_add_sync(kFull, packed[i]);
+        if (lane == 0) reinterpret_cast<uint32_t *>(scratch)[i] = s;
+    }
+    __syncwarp();
+
+    // ---- 5. storage choice (Sec. 3.3), record size, offset (Sec. 3.4) --------------------------
+    uint32_t cost = 0;
+    bool dense_lo = false, dense_hi = false;
+    if (lane < w) {                              // plane `lane`
+        const uint32_t nz = scratch[lane];
+        const bool sparse = (row_bytes - nz) > cols / 64u;           // tie -> dense (R10)
+        cost += sparse ? cols / 64u + nz : row_bytes;
+        dense_lo = !sparse;
+    }
+    if (F64 && lane + 32 < w) {                  // plane `lane + 32`
+        const uint32_t nz = scratch[lane + 32];
+        const bool sparse = (row_bytes - nz) > cols / 64u;
+        cost += sparse ? cols / 64u + nz : row_bytes;
+        dense_hi = !sparse;
+    }
+    const uint32_t body = __reduce_add_sync(kFull, cost);
+    const uint64_t dense_mask = (uint64_t)__ballot_sync(kFull, dense_lo) |
+                                ((uint64_t)__ballot_sync(kFull, dense_hi) << 32);
     const uint32_t flag_bytes = ((uint32_t)w + 7u) / 8u;
     const uint32_t hdr = 3u + T::Z1B + flag_bytes;
     const uint32_t size = hdr + body;
 
-    // ---- 5. output offset (decoupled look-back) ---------------------------------------
     bool ok;
     const uint64_t excl = lookback(job.flags, c, size, lane, ctl, ok);
     if (!ok) {
@@ -266,7 +329,7 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *wsm, int lan
     }
     const uint64_t rec_off = data_start + excl;
     if (c + 1 == job.nchunks && lane == 0) job.result[0] = rec_off + size;
-    if (rec_off + size > job.out_cap) {         // also covers the header and size array
+    if (rec_off + size > job.out_cap) {          // also covers the header and size array
         if (lane == 0) set_status(job.result, kErrCapacity);
         return;
     }
@@ -274,8 +337,10 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *wsm, int lan
     uint8_t *gdst = job.out + rec_off;
     const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(gdst) & 15u);
 
-    // ---- 6. assemble the record in shared memory -------------------------------------
-    RecordWriter wr{wsm, sh, 0u, 0u};
+    // ---- 6. record in shared memory (in place of the consumed plane words), then global ------
+    // Row r (plane w-r) ends before byte 37 + 128 r of the buffer while the plane read next
+    // starts at kPlOff + (64 - w + r) * 128 >= 48 + 128 r: nothing unread is overwritten.
+    RecordWriter wr{buf, sh, 0u, 0u};
     if ((uint32_t)lane < hdr) {
         uint32_t byte;
         const int i = lane;
@@ -284,61 +349,49 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *wsm, int lan
         else if (i < 2 + T::Z1B) byte = (uint32_t)((uint64_t)z1 >> (8 * (i - 2))) & 0xFFu;
         else if (i == 2 + T::Z1B) byte = (uint32_t)w;
         else byte = (uint32_t)(dense_mask >> (8u * (flag_bytes - 1u - (uint32_t)(i - 3 - T::Z1B)))) & 0xFFu;
-        wsm[sh + i] = (uint8_t)byte;
+        buf[sh + i] = (uint8_t)byte;
     }
     wr.pos = hdr;
-    wr.reload(lane);
-#pragma unroll
-    for (int p = T::W - 1; p >= 0; --p) {
-        if (p < w) {
-            if ((dense_mask >> p) & 1ull) wr.dense(FALCON_PLANE(p), lane, nact);
-            else wr.sparse(FALCON_PLANE(p), lane, nact);
-        }
+    wr.reload();
+#pragma unroll 1
+    for (int p = w - 1; p >= 0; --p) {
+        const uint32_t x = *reinterpret_cast<const uint32_t *>(buf + kPlOff + (T::W - 1 - p) * 128 + 4 * lane);
+        if ((dense_mask >> p) & 1ull) wr.dense(x, lane, nact);
+        else wr.sparse(x, lane, nact);
     }
     wr.flush(lane);
-#undef FALCON_PLANE
 
-    // ---- 7. copy to global: aligned 16-byte units, byte stores at the two ends -------
     uint8_t *gbase = gdst - sh;
     const uint32_t total = sh + size;
     const uint32_t units = (total + 15u) / 16u;
     for (uint32_t u = lane; u < units; u += 32) {
         const uint32_t lo = 16u * u, hi = lo + 16u;
         if (lo >= sh && hi <= total) {
-            *reinterpret_cast<uint4 *>(gbase + lo) = *reinterpret_cast<const uint4 *>(wsm + lo);
+            *reinterpret_cast<uint4 *>(gbase + lo) = *reinterpret_cast<const uint4 *>(buf + lo);
         } else {
             const uint32_t b0 = lo > sh ? lo : sh;
             const uint32_t b1 = hi < total ? hi : total;
-            for (uint32_t b = b0; b < b1; ++b) gbase[b] = wsm[b];
+            for (uint32_t b = b0; b < b1; ++b) gbase[b] = buf[b];
         }
     }
-    // the stream header, once per job
-    if (c == 0 && lane == 0) {
-        uint32_t h[8];
-        h[0] = 0x4E434C46u;                                    // "FLCN"
-        h[1] = 1u | ((uint32_t)(F64 ? 0 : 1) << 8);
-        h[2] = B;
-        h[3] = 0;
-        h[4] = (uint32_t)job.n;
-        h[5] = (uint32_t)(job.n >> 32);
-        h[6] = (uint32_t)job.nchunks;
-        h[7] = (uint32_t)(job.nchunks >> 32);
+    if (c == 0 && lane == 0) {                   // the stream header, once per job
         uint4 *dst = reinterpret_cast<uint4 *>(job.out);
-        dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
-        dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+        dst[0] = make_uint4(0x4E434C46u, 1u | ((uint32_t)(F64 ? 0 : 1) << 8), B, 0u);
+        dst[1] = make_uint4((uint32_t)job.n, (uint32_t)(job.n >> 32), (uint32_t)job.nchunks,
+                            (uint32_t)(job.nchunks >> 32));
     }
     __syncwarp();
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 4)
-compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks,
-                Control *ctl) {
+__global__ void __launch_bounds__(kThreads, 3)
+compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint8_t *wsm = smem + warp * kWarpSmem;
+    uint8_t *wbase = smem + warp * kWarpBytes;
+    uint8_t *scratch = wbase + 2 * kBuf;
 
     // jobs without chunks (n = 0) still get a header and a length
     {
@@ -361,18 +414,32 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
     }
 
     int hint64 = -1, hint32 = -1;
-    while (true) {
-        uint64_t t = 0;
-        if (lane == 0) t = atomicAdd(&ctl->ticket, 1ull);
-        t = shfl_u64(t, 0);
-        if (t >= total_chunks) break;
+    int cur = 0;
+    uint64_t t = 0;
+    if (lane == 0) t = atomicAdd(&ctl->ticket, 1ull);
+    t = shfl_u64(t, 0);
+    if (t < total_chunks) issue_chunk(jobs, njobs, single, t, wbase, lane);
+    cp_async_commit();
+    while (t < total_chunks) {
+        uint64_t tn = 0;
+        if (lane == 0) tn = atomicAdd(&ctl->ticket, 1ull);
+        tn = shfl_u64(tn, 0);
+        if (tn < total_chunks) issue_chunk(jobs, njobs, single, tn, wbase + (cur ^ 1) * kBuf, lane);
+        cp_async_commit();
+        cp_async_wait_prior();                   // the current chunk has landed
+        __syncwarp();
         if (*reinterpret_cast<volatile unsigned int *>(&ctl->abort)) break;
         const Job &job = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
         const uint64_t c = t - job.chunk_begin;
-        if (job.dtype == 0) compress_chunk<true>(job, c, wsm, lane, hint64, ctl);
-        else compress_chunk<false>(job, c, wsm, lane, hint32, ctl);
+        if (job.dtype == 0) compress_chunk<true>(job, c, wbase + cur * kBuf, scratch, lane, hint64, ctl);
+        else compress_chunk<false>(job, c, wbase + cur * kBuf, scratch, lane, hint32, ctl);
+        t = tn;
+        cur ^= 1;
     }
+    cp_async_wait_none();
 }
+
+constexpr int kCompressCtaSmem = kWarpsPerCta * kWarpBytes;
 
 static int g_grid_cache[64] = {0};
 
@@ -381,9 +448,10 @@ int compress_grid(uint64_t total_chunks) {
     cudaGetDevice(&dev);
     int &cached = g_grid_cache[dev & 63];
     if (cached == 0) {
+        cudaFuncSetAttribute(compress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCompressCtaSmem);
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, compress_kernel, kThreads, kCtaSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, compress_kernel, kThreads, kCompressCtaSmem);
         cached = sms * (occ > 0 ? occ : 1);
     }
     const uint64_t need = (total_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
@@ -393,7 +461,7 @@ int compress_grid(uint64_t total_chunks) {
 cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,
                             Control *ctl, cudaStream_t stream) {
     const int grid = compress_grid(total_chunks);
-    compress_kernel<<<grid, kThreads, kCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+    compress_kernel<<<grid, kThreads, kCompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
     return cudaGetLastError();
 }
 

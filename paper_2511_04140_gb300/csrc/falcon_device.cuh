@@ -69,9 +69,10 @@ __device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most the most recently committed group is still in flight
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_none() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ uint64_t zigzag(uint64_t x) { return (x << 1) ^ (uint64_t)((int64_t)x >> 63); }
 __device__ __forceinline__ uint32_t zigzag(uint32_t x) { return (x << 1) ^ (uint32_t)((int32_t)x >> 31); }
@@ -176,9 +177,10 @@ __device__ __forceinline__ uint32_t phys_elem_byte(uint32_t e) {
     return phys_unit<F64>(e / PER) * 16u + (e % PER) * S;
 }
 
-// Loads m values (m <= 1025) from global src into the warp's staging buffer.
+// Starts loading m values (m <= 1025) from global src into a warp staging buffer
+// (cp.async; the caller commits and waits).
 template <bool F64>
-__device__ __forceinline__ void stage_values(const uint8_t *src, uint32_t m, uint8_t *wsm, int lane) {
+__device__ __forceinline__ void stage_values_async(const uint8_t *src, uint32_t m, uint8_t *wsm, int lane) {
     constexpr int S = Traits<F64>::S;
     const uint32_t base = smem_addr(wsm);
     const uint32_t nbytes = m * S;
@@ -192,8 +194,6 @@ __device__ __forceinline__ void stage_values(const uint8_t *src, uint32_t m, uin
         if constexpr (F64) cp_async8(base + phys_elem_byte<F64>(e), src + (size_t)e * S);
         else cp_async4(base + phys_elem_byte<F64>(e), src + (size_t)e * S);
     }
-    cp_async_wait_all();
-    __syncwarp();
 }
 
 // Lane reads its 32 values (indices 32*lane + k); indices >= m read as +0.
