@@ -186,7 +186,8 @@ int falcon_stream_info(const void *h_header, size_t len, uint64_t *n, int *dtype
 }
 
 size_t falcon_workspace_bytes(uint64_t nchunks) {
-    return kControlBytes + ((8 * (size_t)nchunks + 255) / 256) * 256;
+    const size_t words = (size_t)(nchunks + (nchunks + 31) / 32);
+    return kControlBytes + ((8 * words + 255) / 256) * 256;
 }
 
 int falcon_compress(const void *d_in, uint64_t n, int dtype, uint32_t block_size, void *d_out,

@@ -322,7 +322,7 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *buf, uint8_t
     const uint32_t size = hdr + body;
 
     bool ok;
-    const uint64_t excl = lookback(job.flags, c, size, lane, ctl, ok);
+    const uint64_t excl = lookback(job.flags, job.flags + job.nchunks, c, job.nchunks, size, lane, ctl, ok);
     if (!ok) {
         if (lane == 0) set_status(job.result, kErrTimeout);
         return;

@@ -66,7 +66,7 @@ __device__ void prepare(const Job &job, uint64_t t, uint8_t *rbuf, int lane, Con
     size = __shfl_sync(kFull, size, 0);
     pd.t = t;
     pd.size = size;
-    const uint64_t excl = lookback(job.flags, c, size, lane, ctl, pd.ok);
+    const uint64_t excl = lookback(job.flags, job.flags + job.nchunks, c, job.nchunks, size, lane, ctl, pd.ok);
     if (!pd.ok) return;
     pd.rec_off = data_start + excl;
     pd.bad = (size < 3u + z1b) || (size > max_rec) || (pd.rec_off + size > job.in_bytes) ||
