@@ -22,66 +22,58 @@ namespace {
 
 constexpr int kBuf = 8256;                  // one chunk of values / one record
 constexpr int kScratch = 128;
-constexpr int kWarpBytes = 2 * kBuf + kScratch;
+constexpr int kWarpBytes = kBuf + kScratch;
 constexpr int kPlOff = 48;                  // plane words: kPlOff + (W-1-p)*128 + 4*lane
 
-// Byte-stream writer over a warp's shared-memory record buffer.  Bytes before `pos` are
-// final in shared memory except the partial 32-bit word at (sh + pos) & ~3, whose valid
-// low bytes are kept, top-aligned, in `pend` (identical in every lane).
-struct RecordWriter {
-    uint8_t *buf;
-    uint32_t sh;
-    uint32_t pos;
-    uint32_t pend;
-
-    __device__ __forceinline__ void reload() {
-        __syncwarp();
-        const uint32_t P = sh + pos;
-        const uint32_t s = P & 3u;
-        pend = s ? (*reinterpret_cast<const uint32_t *>(buf + (P - s)) << (32u - 8u * s)) : 0u;
-    }
-    __device__ __forceinline__ void flush(int lane) {
-        const uint32_t P = sh + pos;
-        const uint32_t s = P & 3u;
-        if (lane == 0 && s) *reinterpret_cast<uint32_t *>(buf + (P - s)) = pend >> (32u - 8u * s);
-        __syncwarp();
-    }
-    // dense row: lane l < nact holds row bytes 4l .. 4l+3 (little-endian) in x
-    __device__ __forceinline__ void dense(uint32_t x, int lane, uint32_t nact) {
-        const uint32_t P = sh + pos;
-        const uint32_t s = P & 3u;
-        uint32_t prev = __shfl_up_sync(kFull, x, 1);
-        if (lane == 0) prev = pend;
-        const uint32_t word = __funnelshift_l(prev, x, 8u * s);
-        if ((uint32_t)lane < nact) *reinterpret_cast<uint32_t *>(buf + (P - s) + 4u * lane) = word;
-        pend = __shfl_sync(kFull, x, (int)nact - 1);
-        pos += 4u * nact;
-    }
-    // sparse row: bitmap of nact/2 bytes, then the non-zero bytes in row order
-    __device__ __forceinline__ void sparse(uint32_t x, int lane, uint32_t nact) {
-        flush(lane);
-        const uint32_t P = sh + pos;
-        const bool active = (uint32_t)lane < nact;
-        const uint32_t nib = active ? nonzero_nibble(x) : 0u;
-        const uint32_t nib_next = __shfl_down_sync(kFull, nib, 1);
-        if (active && !(lane & 1)) buf[P + (lane >> 1)] = (uint8_t)((nib << 4) | nib_next);
-        const uint32_t cnt = __popc(nib);
-        const unsigned b0 = __ballot_sync(kFull, cnt & 1u);
-        const unsigned b1 = __ballot_sync(kFull, cnt & 2u);
-        const unsigned b2 = __ballot_sync(kFull, cnt & 4u);
-        const unsigned lt = (1u << lane) - 1u;
-        const uint32_t before = __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt);
-        const uint32_t total = __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2);
-        uint32_t q = P + nact / 2u + before;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t byte = (x >> (8 * i)) & 0xFFu;
-            if (active && byte) buf[q++] = (uint8_t)byte;
+// Moves len bytes from src to dst (byte offsets in the warp buffer, dst <= src) with
+// aligned 32-bit stores.  Bytes before dst in its first word are preserved; the bytes after
+// dst + len in the last word are overwritten (the caller keeps >= 4 free bytes there).
+// Reads run ahead of writes in every iteration, so the overlap dst < src is safe.
+__device__ __forceinline__ void smem_move_down(uint8_t *buf, uint32_t dst, uint32_t src, uint32_t len, int lane) {
+    const uint32_t d0 = dst & ~3u;
+    const uint32_t head = dst & 3u;
+    const uint32_t nwords = (head + len + 3u) >> 2;
+    const uint32_t shift = src - dst;
+    for (uint32_t j = lane; j < nwords; j += 32) {
+        const uint32_t a = d0 + 4u * j;
+        const uint32_t sa = a + shift;                  // source byte of this word's byte 0
+        const uint32_t s = sa & 3u;
+        const uint32_t *w = reinterpret_cast<const uint32_t *>(buf + (sa - s));
+        uint32_t word = __funnelshift_r(w[0], w[1], 8u * s);
+        if (j == 0 && head) {
+            const uint32_t keep = (1u << (8u * head)) - 1u;
+            word = (word & ~keep) | (*reinterpret_cast<const uint32_t *>(buf + a) & keep);
         }
-        pos += nact / 2u + total;
-        reload();
+        __syncwarp(__activemask());
+        *reinterpret_cast<uint32_t *>(buf + a) = word;
     }
-};
+    __syncwarp();
+}
+
+// Sparse row (Sec. 3.3) written with byte stores at byte offset P of the warp buffer:
+// a bitmap of nact/2 bytes (bit 7 of byte 0 = row byte 0), then the non-zero row bytes.
+// Returns the row's length.
+__device__ __forceinline__ uint32_t sparse_row(uint8_t *buf, uint32_t P, uint32_t x, int lane, uint32_t nact) {
+    const bool active = (uint32_t)lane < nact;
+    const uint32_t nib = active ? nonzero_nibble(x) : 0u;
+    const uint32_t nib_next = __shfl_down_sync(kFull, nib, 1);
+    if (active && !(lane & 1)) buf[P + (lane >> 1)] = (uint8_t)((nib << 4) | nib_next);
+    const uint32_t cnt = __popc(nib);
+    const unsigned b0 = __ballot_sync(kFull, cnt & 1u);
+    const unsigned b1 = __ballot_sync(kFull, cnt & 2u);
+    const unsigned b2 = __ballot_sync(kFull, cnt & 4u);
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t before = __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt);
+    const uint32_t total = __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2);
+    uint32_t q = P + nact / 2u + before;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t byte = (x >> (8 * i)) & 0xFFu;
+        if (active && byte) buf[q++] = (uint8_t)byte;
+    }
+    __syncwarp();
+    return nact / 2u + total;
+}
 
 // value k of this lane from the swizzled staging buffer
 template <bool F64>
@@ -199,18 +191,20 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *buf, uint8_t
             const int e_max = floor_log10(vmax);
             const int atop = min(T::A_MAX, T::B_MAX - 1 - e_max);
             if (atop >= 0) {
-                // quick rejection: Alg. 2 on the largest magnitude(s) first
-                bool fail = false;
+                // quick rejection: Alg. 2 on the largest magnitude first (one per lane)
+                U cand = 0;
+                bool has = (vx & ABS) == vmax;
+                if (has) cand = vx;
 #pragma unroll
                 for (int k = 0; k < 32; ++k) {
-                    if ((v[k] & ABS) == vmax) {
-                        if constexpr (F64) fail |= !q_test(v[k], atop);
-                        else fail |= first_pass_f32(v[k], atop) < 0;
-                    }
+                    const bool is_max = (v[k] & ABS) == vmax;
+                    cand = is_max ? v[k] : cand;
+                    has |= is_max;
                 }
-                if ((vx & ABS) == vmax) {
-                    if constexpr (F64) fail |= !q_test(vx, atop);
-                    else fail |= first_pass_f32(vx, atop) < 0;
+                bool fail = false;
+                if (has) {
+                    if constexpr (F64) fail = !q_test(cand, atop);
+                    else fail = first_pass_f32(cand, atop) < 0;
                 }
                 if (!__any_sync(kFull, fail)) {
                     if constexpr (F64) alpha = search_alpha64(buf, lane, m, vx, atop, hint);
@@ -340,7 +334,6 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *buf, uint8_t
     // ---- 6. record in shared memory (in place of the consumed plane words), then global ------
     // Row r (plane w-r) ends before byte 37 + 128 r of the buffer while the plane read next
     // starts at kPlOff + (64 - w + r) * 128 >= 48 + 128 r: nothing unread is overwritten.
-    RecordWriter wr{buf, sh, 0u, 0u};
     if ((uint32_t)lane < hdr) {
         uint32_t byte;
         const int i = lane;
@@ -351,15 +344,33 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *buf, uint8_t
         else byte = (uint32_t)(dense_mask >> (8u * (flag_bytes - 1u - (uint32_t)(i - 3 - T::Z1B)))) & 0xFFu;
         buf[sh + i] = (uint8_t)byte;
     }
-    wr.pos = hdr;
-    wr.reload();
-#pragma unroll 1
-    for (int p = w - 1; p >= 0; --p) {
-        const uint32_t x = *reinterpret_cast<const uint32_t *>(buf + kPlOff + (T::W - 1 - p) * 128 + 4 * lane);
-        if ((dense_mask >> p) & 1ull) wr.dense(x, lane, nact);
-        else wr.sparse(x, lane, nact);
+    __syncwarp();
+    uint32_t pos = sh + hdr;                      // next record byte in the buffer
+    int p = w - 1;
+    while (p >= 0) {
+        const uint32_t src = kPlOff + (uint32_t)(T::W - 1 - p) * 128u;
+        if ((dense_mask >> p) & 1ull) {
+            // a run of dense rows p, p-1, ... : contiguous in the plane buffer when rows are
+            // 128 bytes long, so one shifted move copies the whole run
+            int q = p;
+            if (row_bytes == 128u)
+                while (q > 0 && ((dense_mask >> (q - 1)) & 1ull)) --q;
+            const uint32_t rows = (uint32_t)(p - q + 1);
+            if (row_bytes == 128u) {
+                smem_move_down(buf, pos, src, rows * 128u, lane);
+            } else {
+                smem_move_down(buf, pos, src, row_bytes, lane);
+            }
+            pos += rows * row_bytes;
+            p = q - 1;
+        } else {
+            const uint32_t x = *reinterpret_cast<const uint32_t *>(buf + src + 4 * lane);
+            __syncwarp();
+            pos += sparse_row(buf, pos, x, lane, nact);
+            --p;
+        }
     }
-    wr.flush(lane);
+    __syncwarp();
 
     uint8_t *gbase = gdst - sh;
     const uint32_t total = sh + size;
@@ -385,13 +396,13 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *buf, uint8_t
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, 4)
 compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     uint8_t *wbase = smem + warp * kWarpBytes;
-    uint8_t *scratch = wbase + 2 * kBuf;
+    uint8_t *scratch = wbase + kBuf;
 
     // jobs without chunks (n = 0) still get a header and a length
     {
@@ -414,29 +425,21 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
     }
 
     int hint64 = -1, hint32 = -1;
-    int cur = 0;
-    uint64_t t = 0;
-    if (lane == 0) t = atomicAdd(&ctl->ticket, 1ull);
-    t = shfl_u64(t, 0);
-    if (t < total_chunks) issue_chunk(jobs, njobs, single, t, wbase, lane);
-    cp_async_commit();
-    while (t < total_chunks) {
-        uint64_t tn = 0;
-        if (lane == 0) tn = atomicAdd(&ctl->ticket, 1ull);
-        tn = shfl_u64(tn, 0);
-        if (tn < total_chunks) issue_chunk(jobs, njobs, single, tn, wbase + (cur ^ 1) * kBuf, lane);
-        cp_async_commit();
-        cp_async_wait_prior();                   // the current chunk has landed
-        __syncwarp();
+    while (true) {
+        uint64_t t = 0;
+        if (lane == 0) t = atomicAdd(&ctl->ticket, 1ull);
+        t = shfl_u64(t, 0);
+        if (t >= total_chunks) break;
         if (*reinterpret_cast<volatile unsigned int *>(&ctl->abort)) break;
         const Job &job = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
         const uint64_t c = t - job.chunk_begin;
-        if (job.dtype == 0) compress_chunk<true>(job, c, wbase + cur * kBuf, scratch, lane, hint64, ctl);
-        else compress_chunk<false>(job, c, wbase + cur * kBuf, scratch, lane, hint32, ctl);
-        t = tn;
-        cur ^= 1;
+        issue_chunk(jobs, njobs, single, t, wbase, lane);
+        cp_async_commit();
+        cp_async_wait_none();
+        __syncwarp();
+        if (job.dtype == 0) compress_chunk<true>(job, c, wbase, scratch, lane, hint64, ctl);
+        else compress_chunk<false>(job, c, wbase, scratch, lane, hint32, ctl);
     }
-    cp_async_wait_none();
 }
 
 constexpr int kCompressCtaSmem = kWarpsPerCta * kWarpBytes;
