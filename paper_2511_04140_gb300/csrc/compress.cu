@@ -22,7 +22,7 @@ namespace {
 
 constexpr int kBuf = 8256;                  // one chunk of values / one record
 constexpr int kScratch = 128;
-constexpr int kWarpBytes = kBuf + kScratch;
+constexpr int kWarpBytes = 2 * kBuf + kScratch;
 constexpr int kPlOff = 48;                  // plane words: kPlOff + (W-1-p)*128 + 4*lane
 
 // Moves len bytes from src to dst (byte offsets in the warp buffer, dst <= src) with
@@ -152,9 +152,24 @@ __device__ __forceinline__ void issue_chunk(const Job *jobs, int njobs, const Jo
     else stage_values_async<false>(job.in + first * 4u, m, buf, lane);
 }
 
+// A chunk whose size is published and whose record waits for its offset.
+struct Pend {
+    uint64_t t;             // global ticket
+    uint64_t z1;
+    uint64_t dense_mask;
+    uint32_t size;
+    int w;
+    int alpha_byte;         // header byte 0 (alpha_max or the Case-2 sentinel)
+    int beta_hat;           // header byte 1
+    bool valid;
+};
+
+// Steps 1-5: everything up to the record size, which is published for the look-back.
+// The plane words stay in buf for finish_chunk.
 template <bool F64>
-__device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *buf, uint8_t *scratch, int lane,
-                               int &hint, Control *ctl) {
+__device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t *scratch, int lane,
+                              int &hint, Pend &pd) {
+    const uint64_t c = t - job.chunk_begin;
     using T = Traits<F64>;
     using U = typename T::U;
     constexpr U ABS = F64 ? (U)0x7FFFFFFFFFFFFFFFull : (U)0x7FFFFFFFu;
@@ -314,18 +329,48 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *buf, uint8_t
     const uint32_t flag_bytes = ((uint32_t)w + 7u) / 8u;
     const uint32_t hdr = 3u + T::Z1B + flag_bytes;
     const uint32_t size = hdr + body;
+    publish_size(job.flags, c, size, lane);
+    pd.t = t;
+    pd.z1 = (uint64_t)z1;
+    pd.dense_mask = dense_mask;
+    pd.size = size;
+    pd.w = w;
+    pd.alpha_byte = alpha >= 0 ? alpha : T::A_SENT;
+    pd.beta_hat = beta_hat;
+    pd.valid = true;
+    (void)data_start;
+}
+
+// Steps 5-6 of a computed chunk: offset (look-back), record assembly in place of its plane
+// words, and the copy to global memory.  Returns false when a bounded wait gave up.
+template <bool F64>
+__device__ bool finish_chunk(const Job &job, const Pend &pd, uint8_t *buf, int lane, Control *ctl) {
+    using T = Traits<F64>;
+    const uint64_t c = pd.t - job.chunk_begin;
+    const uint32_t B = job.block;
+    const uint64_t first = c * (uint64_t)B;
+    const uint32_t m = (uint32_t)((job.n - first) < B ? (job.n - first) : B);
+    const uint64_t data_start = 32ull + 4ull * job.nchunks;
+    const uint32_t cols = chunk_cols(m);
+    const uint32_t nact = cols / 32u;
+    const uint32_t row_bytes = cols / 8u;
+    const int w = pd.w;
+    const uint32_t size = pd.size;
+    const uint64_t dense_mask = pd.dense_mask;
+    const uint32_t flag_bytes = ((uint32_t)w + 7u) / 8u;
+    const uint32_t hdr = 3u + T::Z1B + flag_bytes;
 
     bool ok;
     const uint64_t excl = lookback(job.flags, job.flags + job.nchunks, c, job.nchunks, size, lane, ctl, ok);
     if (!ok) {
         if (lane == 0) set_status(job.result, kErrTimeout);
-        return;
+        return false;
     }
     const uint64_t rec_off = data_start + excl;
     if (c + 1 == job.nchunks && lane == 0) job.result[0] = rec_off + size;
     if (rec_off + size > job.out_cap) {          // also covers the header and size array
         if (lane == 0) set_status(job.result, kErrCapacity);
-        return;
+        return true;
     }
     if (lane == 0) *reinterpret_cast<uint32_t *>(job.out + 32 + 4 * c) = size;
     uint8_t *gdst = job.out + rec_off;
@@ -337,9 +382,9 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *buf, uint8_t
     if ((uint32_t)lane < hdr) {
         uint32_t byte;
         const int i = lane;
-        if (i == 0) byte = (uint32_t)(alpha >= 0 ? alpha : T::A_SENT);
-        else if (i == 1) byte = (uint32_t)beta_hat;
-        else if (i < 2 + T::Z1B) byte = (uint32_t)((uint64_t)z1 >> (8 * (i - 2))) & 0xFFu;
+        if (i == 0) byte = (uint32_t)pd.alpha_byte;
+        else if (i == 1) byte = (uint32_t)pd.beta_hat;
+        else if (i < 2 + T::Z1B) byte = (uint32_t)(pd.z1 >> (8 * (i - 2))) & 0xFFu;
         else if (i == 2 + T::Z1B) byte = (uint32_t)w;
         else byte = (uint32_t)(dense_mask >> (8u * (flag_bytes - 1u - (uint32_t)(i - 3 - T::Z1B)))) & 0xFFu;
         buf[sh + i] = (uint8_t)byte;
@@ -392,17 +437,18 @@ __device__ void compress_chunk(const Job &job, uint64_t c, uint8_t *buf, uint8_t
                             (uint32_t)(job.nchunks >> 32));
     }
     __syncwarp();
+    return true;
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, 3)
 compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     uint8_t *wbase = smem + warp * kWarpBytes;
-    uint8_t *scratch = wbase + kBuf;
+    uint8_t *scratch = wbase + 2 * kBuf;
 
     // jobs without chunks (n = 0) still get a header and a length
     {
@@ -424,7 +470,12 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
         }
     }
 
+    // Two-stage pipeline per warp: chunk t is computed and its size published before the
+    // previous chunk's offset is resolved, so the look-back waits overlap useful work.
     int hint64 = -1, hint32 = -1;
+    int cur = 0;
+    Pend pend;
+    pend.valid = false;
     while (true) {
         uint64_t t = 0;
         if (lane == 0) t = atomicAdd(&ctl->ticket, 1ull);
@@ -432,13 +483,27 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
         if (t >= total_chunks) break;
         if (*reinterpret_cast<volatile unsigned int *>(&ctl->abort)) break;
         const Job &job = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
-        const uint64_t c = t - job.chunk_begin;
-        issue_chunk(jobs, njobs, single, t, wbase, lane);
+        uint8_t *buf = wbase + cur * kBuf;
+        issue_chunk(jobs, njobs, single, t, buf, lane);
         cp_async_commit();
         cp_async_wait_none();
         __syncwarp();
-        if (job.dtype == 0) compress_chunk<true>(job, c, wbase, scratch, lane, hint64, ctl);
-        else compress_chunk<false>(job, c, wbase, scratch, lane, hint32, ctl);
+        Pend next;
+        if (job.dtype == 0) compute_chunk<true>(job, t, buf, scratch, lane, hint64, next);
+        else compute_chunk<false>(job, t, buf, scratch, lane, hint32, next);
+        if (pend.valid) {
+            const Job &pj = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, pend.t)];
+            const bool ok = (pj.dtype == 0) ? finish_chunk<true>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl)
+                                            : finish_chunk<false>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl);
+            if (!ok) return;
+        }
+        pend = next;
+        cur ^= 1;
+    }
+    if (pend.valid) {
+        const Job &pj = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, pend.t)];
+        if (pj.dtype == 0) finish_chunk<true>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl);
+        else finish_chunk<false>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl);
     }
 }
 

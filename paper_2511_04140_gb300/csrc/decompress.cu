@@ -1,15 +1,18 @@
-// Falcon decompression kernel (Sec. 4 of the paper) for sm_103a.
+// Falcon decompression (Sec. 4 of the paper) for sm_103a: two launches per call.
 //
-// Persistent launch, one warp per chunk (dynamic ticket).  A warp prepares chunk t+1 (reads
-// its size, decoupled look-back for its offset, starts the cp.async of its record) before it
-// decodes chunk t, so record loads overlap decoding.  Decoding a chunk:
-//   1. parse the header and flags; every row is expanded into one 32-bit word per lane
-//      (dense: an unaligned 4-byte read; sparse: bitmap nibble + popcount rank) and stored
-//      in the warp's plane buffer,
-//   2. 32x32 register transposes give Z back; unzigzag + warp scan give G (inverse Eq. 5);
-//      Case 1 divides by 10^alpha (correctly rounded), Case 2 undoes the zigzag of the
-//      IEEE bits (inverse Eq. 4),
-//   3. values are staged (swizzled) and written with coalesced 16-byte stores.
+// 1. offsets_kernel: the chunk-size array is read and its exclusive prefix (the chunk
+//    offset array) is written to the workspace - the step Sec. 4 performs first.
+// 2. decompress_kernel: persistent; warp w decodes chunks w, w + W, w + 2W, ... (no
+//    ordering constraint remains).  Each warp starts the cp.async of its next record
+//    before decoding the current one; offsets are loaded one step earlier still.
+//    Decoding a record:
+//      a. header and flags; a walk over the rows that touches only sparse rows' bitmaps
+//         gives every row's position; sparse rows are expanded into the plane buffer,
+//      b. all plane words are gathered (dense rows straight from the record) into
+//         registers, two 32x32 transposes give Z, unzigzag + warp scan give G
+//         (inverse Eq. 5), Case 1 divides by 10^alpha (correctly rounded) and Case 2
+//         undoes the zigzag of the IEEE bits (inverse Eq. 4),
+//      c. values are staged (swizzled) and written with coalesced 16-byte stores.
 // Every read of a record is bounds-checked against its size; a malformed record sets
 // FALCON_ERR_CORRUPT and writes nothing.
 #include "falcon_device.cuh"
@@ -18,8 +21,9 @@ namespace falcon {
 
 namespace {
 
-constexpr int kBuf = 8256;
-constexpr int kWarpBytes = 3 * kBuf;        // two record buffers + plane / value buffer
+constexpr int kBuf = 8256;                  // one record (<= 8211 bytes at a 0..15 phase)
+constexpr int kPlane = 8192 + 128;          // 64 plane rows of 128 bytes + 64 u16 row positions
+constexpr int kWarpBytes = 2 * kBuf + kPlane;
 
 // unaligned little-endian 32-bit read at byte i of a 16-byte aligned shared buffer
 __device__ __forceinline__ uint32_t ld_u32_unaligned(const uint8_t *b, uint32_t i) {
@@ -35,48 +39,44 @@ __device__ __forceinline__ float div_pow10(int32_t g, int a) {
     return __fdiv_rn(__int2float_rn(g), __uint_as_float(FALCON_P10_F32[a - FALCON_P10_F32_LO]));
 }
 
-// A chunk whose record is on its way into shared memory.
-struct Pending {
-    uint64_t t;          // global ticket
-    uint64_t rec_off;    // record offset in the stream
-    uint32_t size;       // record bytes
-    uint32_t sh;         // 16-byte phase of the record in global (and shared) memory
-    bool bad;            // size/offset inconsistent with the stream
-    bool ok;             // look-back completed
-};
-
 __device__ __forceinline__ const Job &job_of(const Job *jobs, int njobs, const Job &single, uint64_t t) {
     return (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
 }
 
-// Size, offset and record load of ticket t (no wait).
-__device__ void prepare(const Job &job, uint64_t t, uint8_t *rbuf, int lane, Control *ctl, Pending &pd) {
-    const uint64_t c = t - job.chunk_begin;
-    const uint32_t B = job.block;
-    const uint64_t first = c * (uint64_t)B;
-    const uint32_t m = (uint32_t)((job.n - first) < B ? (job.n - first) : B);
-    const uint32_t cols = chunk_cols(m);
-    const uint32_t W = job.dtype == 0 ? 64u : 32u;
-    const uint32_t z1b = W / 8u;
-    const uint32_t max_rec = 3u + z1b + W / 8u + W * (cols / 8u);
-    const uint64_t data_start = 32ull + 4ull * job.nchunks;
+// Offset (within the stream) and size of the record of ticket t, loaded early.
+struct Loc {
+    uint64_t t;
+    uint64_t rec_off;
+    uint32_t size;
+};
 
-    uint32_t size = 0;
-    if (lane == 0) size = *reinterpret_cast<const uint32_t *>(job.in + 32 + 4 * c);
-    size = __shfl_sync(kFull, size, 0);
-    pd.t = t;
-    pd.size = size;
-    const uint64_t excl = lookback(job.flags, job.flags + job.nchunks, c, job.nchunks, size, lane, ctl, pd.ok);
-    if (!pd.ok) return;
-    pd.rec_off = data_start + excl;
-    pd.bad = (size < 3u + z1b) || (size > max_rec) || (pd.rec_off + size > job.in_bytes) ||
-             (pd.rec_off + size < pd.rec_off);
-    const uint8_t *gsrc = job.in + pd.rec_off;
-    pd.sh = (uint32_t)(reinterpret_cast<uintptr_t>(gsrc) & 15u);
-    if (pd.bad) return;
-    const uint8_t *gbase = gsrc - pd.sh;                       // >= job.in (16-byte aligned)
+__device__ __forceinline__ Loc locate(const Job *jobs, int njobs, const Job &single, uint64_t t) {
+    const Job &job = job_of(jobs, njobs, single, t);
+    const uint64_t c = t - job.chunk_begin;
+    Loc l;
+    l.t = t;
+    l.rec_off = 32ull + 4ull * job.nchunks + reinterpret_cast<const unsigned long long *>(job.flags)[c];
+    l.size = *reinterpret_cast<const uint32_t *>(job.in + 32 + 4 * c);
+    return l;
+}
+
+__device__ __forceinline__ uint32_t max_record(uint32_t m, uint32_t dtype) {
+    const uint32_t W = dtype == 0 ? 64u : 32u;
+    return 3u + W / 8u + W / 8u + W * (chunk_cols(m) / 8u);
+}
+
+// Starts the cp.async of a record into rbuf; returns false if its location is invalid.
+__device__ __forceinline__ bool issue_record(const Job &job, const Loc &l, uint8_t *rbuf, int lane) {
+    const uint64_t c = l.t - job.chunk_begin;
+    const uint64_t first = c * (uint64_t)job.block;
+    const uint32_t m = (uint32_t)((job.n - first) < job.block ? (job.n - first) : job.block);
+    const uint32_t z1b = job.dtype == 0 ? 8u : 4u;
+    if (l.size < 3u + z1b || l.size > max_record(m, job.dtype) || l.rec_off + l.size > job.in_bytes) return false;
+    const uint8_t *gsrc = job.in + l.rec_off;
+    const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(gsrc) & 15u);
+    const uint8_t *gbase = gsrc - sh;                       // >= job.in (16-byte aligned)
     const uint8_t *gend = job.in + job.in_bytes;
-    const uint32_t units = (pd.sh + size + 15u) / 16u;
+    const uint32_t units = (sh + l.size + 15u) / 16u;
     const uint32_t base = smem_addr(rbuf);
     for (uint32_t u = lane; u < units; u += 32) {
         const uint8_t *src = gbase + 16u * u;
@@ -84,26 +84,29 @@ __device__ void prepare(const Job &job, uint64_t t, uint8_t *rbuf, int lane, Con
         else
             for (uint32_t b = 0; b < 16u && src + b < gend; ++b) rbuf[16u * u + b] = src[b];
     }
+    return true;
 }
 
 template <bool F64>
-__device__ void decode_chunk(const Job &job, const Pending &pd, const uint8_t *rbuf, uint8_t *pbuf, int lane) {
+__device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const uint8_t *rbuf, uint8_t *pbuf,
+                             int lane) {
     using T = Traits<F64>;
     using U = typename T::U;
 
-    const uint64_t c = pd.t - job.chunk_begin;
+    const uint64_t c = l.t - job.chunk_begin;
     const uint32_t B = job.block;
     const uint64_t first = c * (uint64_t)B;
     const uint32_t m = (uint32_t)((job.n - first) < B ? (job.n - first) : B);
     const uint32_t cols = chunk_cols(m);
     const uint32_t nact = cols / 32u;
     const uint32_t row_bytes = cols / 8u;
-    const uint32_t size = pd.size;
-    const uint32_t sh = pd.sh;
+    const uint32_t size = l.size;
+    const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(job.in + l.rec_off) & 15u);
     const uint8_t *rec = rbuf + sh;
+    uint16_t *rowpos = reinterpret_cast<uint16_t *>(pbuf + 8192);
 
-    // ---- 1. header, flags, rows -> plane words ---------------------------------------------
-    bool bad = pd.bad;
+    // ---- a. header, flags, row positions; sparse rows expanded ---------------------------
+    bool bad = !loc_ok;
     uint32_t alpha = 0, beta_hat = 0, w = 0, pos = 0;
     U z1 = 0;
     uint64_t dense_mask = 0;
@@ -123,11 +126,10 @@ __device__ void decode_chunk(const Job &job, const Pending &pd, const uint8_t *r
     const uint32_t bm_bytes = nact / 2u;
 #pragma unroll 1
     for (int p = (int)w - 1; p >= 0 && !bad; --p) {
-        uint32_t x = 0;
+        if (lane == 0) rowpos[p] = (uint16_t)pos;
         if ((dense_mask >> p) & 1ull) {
-            if (pos + row_bytes > size) { bad = true; break; }
-            if (active) x = ld_u32_unaligned(rbuf, sh + pos + 4u * lane);
             pos += row_bytes;
+            if (pos > size) bad = true;
         } else {
             if (pos + bm_bytes > size) { bad = true; break; }
             uint32_t nib = 0;
@@ -143,13 +145,13 @@ __device__ void decode_chunk(const Job &job, const Pending &pd, const uint8_t *r
             const uint32_t before = __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt);
             const uint32_t nnz = __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2);
             if (pos + bm_bytes + nnz > size) { bad = true; break; }
-            uint32_t q = pos + bm_bytes + before;
+            uint32_t x = 0, q = pos + bm_bytes + before;
 #pragma unroll
             for (int i = 0; i < 4; ++i)
                 if ((nib >> (3 - i)) & 1u) x |= (uint32_t)rec[q++] << (8 * i);
+            *reinterpret_cast<uint32_t *>(pbuf + p * 128 + 4 * lane) = x;
             pos += bm_bytes + nnz;
         }
-        *reinterpret_cast<uint32_t *>(pbuf + p * 128 + 4 * lane) = x;
     }
     if (pos != size) bad = true;
     if (bad) {
@@ -158,12 +160,22 @@ __device__ void decode_chunk(const Job &job, const Pending &pd, const uint8_t *r
     }
     __syncwarp();
 
-    // ---- 2. Z -> G -> values -------------------------------------------------------------------
+    // ---- b. gather plane words, Z -> G -> values ------------------------------------------
     U d[32];
     {
         uint32_t a[32];
 #pragma unroll
-        for (int p = 0; p < 32; ++p) a[p] = ((uint32_t)p < w) ? *reinterpret_cast<const uint32_t *>(pbuf + p * 128 + 4 * lane) : 0u;
+        for (int p = 0; p < 32; ++p) {
+            uint32_t x = 0;
+            if ((uint32_t)p < w) {
+                if ((dense_mask >> p) & 1ull) {
+                    if (active) x = ld_u32_unaligned(rbuf, sh + rowpos[p] + 4u * lane);
+                } else {
+                    x = *reinterpret_cast<const uint32_t *>(pbuf + p * 128 + 4 * lane);
+                }
+            }
+            a[p] = x;
+        }
         transpose32(a);
 #pragma unroll
         for (int k = 0; k < 32; ++k) d[k] = (U)a[k ^ 7];
@@ -172,8 +184,17 @@ __device__ void decode_chunk(const Job &job, const Pending &pd, const uint8_t *r
         if (w > 32) {
             uint32_t a[32];
 #pragma unroll
-            for (int p = 0; p < 32; ++p)
-                a[p] = ((uint32_t)(p + 32) < w) ? *reinterpret_cast<const uint32_t *>(pbuf + (p + 32) * 128 + 4 * lane) : 0u;
+            for (int p = 0; p < 32; ++p) {
+                uint32_t x = 0;
+                if ((uint32_t)(p + 32) < w) {
+                    if ((dense_mask >> (p + 32)) & 1ull) {
+                        if (active) x = ld_u32_unaligned(rbuf, sh + rowpos[p + 32] + 4u * lane);
+                    } else {
+                        x = *reinterpret_cast<const uint32_t *>(pbuf + (p + 32) * 128 + 4 * lane);
+                    }
+                }
+                a[p] = x;
+            }
             transpose32(a);
 #pragma unroll
             for (int k = 0; k < 32; ++k) d[k] |= (U)a[k ^ 7] << 32;
@@ -214,7 +235,7 @@ __device__ void decode_chunk(const Job &job, const Pending &pd, const uint8_t *r
     d[0] = carry;
     __syncwarp();                                 // plane words consumed
 
-    // ---- 3. stage (swizzled) and store -----------------------------------------------------------
+    // ---- c. stage (swizzled) and store --------------------------------------------------------
     constexpr int UN = T::UNITS;
 #pragma unroll
     for (int u = 0; u < UN; ++u) {
@@ -243,7 +264,57 @@ __device__ void decode_chunk(const Job &job, const Pending &pd, const uint8_t *r
     __syncwarp();
 }
 
+// block-wide exclusive scan of one u64 per thread (1024 threads); returns the block total
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t &total, uint64_t *warp_sums) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t incl = v + warp_exclusive_u64(v, lane);
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t ws = warp_sums[lane];
+        const uint64_t wincl = ws + warp_exclusive_u64(ws, lane);
+        warp_sums[lane] = wincl - ws;
+        if (lane == 31) warp_sums[32] = wincl;
+    }
+    __syncthreads();
+    const uint64_t r = warp_sums[warp] + incl - v;
+    total = warp_sums[32];
+    __syncthreads();
+    return r;
+}
+
 }  // namespace
+
+// Chunk offsets (exclusive prefix of the u32 size array) of every job into job.flags.
+__global__ void __launch_bounds__(1024)
+offsets_kernel(const Job *__restrict__ jobs, Job single) {
+    __shared__ uint64_t warp_sums[33];
+    const Job &job = (jobs == nullptr) ? single : jobs[blockIdx.x];
+    const uint64_t nc = job.nchunks;
+    const uint32_t *sizes = reinterpret_cast<const uint32_t *>(job.in + 32);
+    unsigned long long *off = job.flags;
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < nc; base += 4096) {
+        const uint64_t i0 = base + 4ull * threadIdx.x;
+        uint32_t s[4] = {0, 0, 0, 0};
+        if (i0 + 4 <= nc) {
+            const uint4 q = *reinterpret_cast<const uint4 *>(sizes + i0);
+            s[0] = q.x; s[1] = q.y; s[2] = q.z; s[3] = q.w;
+        } else {
+            for (int k = 0; k < 4; ++k)
+                if (i0 + k < nc) s[k] = sizes[i0 + k];
+        }
+        const uint64_t local = (uint64_t)s[0] + s[1] + s[2] + s[3];
+        uint64_t total;
+        uint64_t ex = carry + block_exclusive_scan(local, total, warp_sums);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < nc) off[i0 + k] = ex;
+            ex += s[k];
+        }
+        carry += total;
+    }
+}
 
 __global__ void __launch_bounds__(kThreads, 2)
 decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
@@ -252,44 +323,37 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
     const int warp = threadIdx.x >> 5;
     uint8_t *wbase = smem + warp * kWarpBytes;
     uint8_t *pbuf = wbase + 2 * kBuf;
-    {
-        const int gw = blockIdx.x * kWarpsPerCta + warp;
-        const int nw = gridDim.x * kWarpsPerCta;
-        const int nj = (jobs != nullptr) ? njobs : 1;
-        for (int j = gw; j < nj; j += nw) {
-            const Job &jb = (jobs != nullptr) ? jobs[j] : single;
-            if (lane == 0) jb.result[0] = jb.n;
-        }
+    const uint64_t gw = (uint64_t)blockIdx.x * kWarpsPerCta + warp;
+    const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
+    (void)ctl;
+    for (uint64_t j = gw; j < (uint64_t)((jobs != nullptr) ? njobs : 1); j += nw) {
+        const Job &jb = (jobs != nullptr) ? jobs[j] : single;
+        if (lane == 0) jb.result[0] = jb.n;
     }
+    if (gw >= total_chunks) return;
     int cur = 0;
-    Pending pd{}, pn{};
-    uint64_t t = 0;
-    if (lane == 0) t = atomicAdd(&ctl->ticket, 1ull);
-    t = shfl_u64(t, 0);
-    if (t < total_chunks) prepare(job_of(jobs, njobs, single, t), t, wbase, lane, ctl, pd);
+    Loc lc = locate(jobs, njobs, single, gw);
+    bool okc = issue_record(job_of(jobs, njobs, single, gw), lc, wbase, lane);
     cp_async_commit();
-    while (t < total_chunks) {
-        uint64_t tn = 0;
-        if (lane == 0) tn = atomicAdd(&ctl->ticket, 1ull);
-        tn = shfl_u64(tn, 0);
-        pn.ok = true;
-        if (tn < total_chunks) prepare(job_of(jobs, njobs, single, tn), tn, wbase + (cur ^ 1) * kBuf, lane, ctl, pn);
+    Loc ln{};
+    if (gw + nw < total_chunks) ln = locate(jobs, njobs, single, gw + nw);
+    for (uint64_t t = gw; t < total_chunks; t += nw) {
+        const uint64_t tn = t + nw;
+        bool okn = false;
+        Loc lnn{};
+        if (tn < total_chunks) {
+            okn = issue_record(job_of(jobs, njobs, single, tn), ln, wbase + (cur ^ 1) * kBuf, lane);
+            if (tn + nw < total_chunks) lnn = locate(jobs, njobs, single, tn + nw);
+        }
         cp_async_commit();
         cp_async_wait_prior();                   // the current record has landed
         __syncwarp();
         const Job &job = job_of(jobs, njobs, single, t);
-        if (!pd.ok) {
-            if (lane == 0) set_status(job.result, kErrTimeout);
-            break;
-        }
-        if (job.dtype == 0) decode_chunk<true>(job, pd, wbase + cur * kBuf, pbuf, lane);
-        else decode_chunk<false>(job, pd, wbase + cur * kBuf, pbuf, lane);
-        if (!pn.ok && tn < total_chunks) {
-            if (lane == 0) set_status(job_of(jobs, njobs, single, tn).result, kErrTimeout);
-            break;
-        }
-        t = tn;
-        pd = pn;
+        if (job.dtype == 0) decode_chunk<true>(job, lc, okc, wbase + cur * kBuf, pbuf, lane);
+        else decode_chunk<false>(job, lc, okc, wbase + cur * kBuf, pbuf, lane);
+        lc = ln;
+        okc = okn;
+        ln = lnn;
         cur ^= 1;
     }
     cp_async_wait_none();
@@ -316,6 +380,7 @@ int decompress_grid(uint64_t total_chunks) {
 
 cudaError_t launch_decompress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,
                               Control *ctl, cudaStream_t stream) {
+    offsets_kernel<<<(d_jobs != nullptr) ? njobs : 1, 1024, 0, stream>>>(d_jobs, single);
     const int grid = decompress_grid(total_chunks);
     decompress_kernel<<<grid, kThreads, kDecompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
     return cudaGetLastError();

@@ -379,6 +379,11 @@ __device__ __forceinline__ uint32_t case1_g(uint32_t u, int a) {
 // chunks per round trip).  Every wait is on lower tickets only, and bounded: on timeout
 // (or when another warp already gave up) it sets ctl->abort and returns ok = false.
 // --------------------------------------------------------------------------------------
+__device__ __forceinline__ void publish_size(unsigned long long *f1, uint64_t c, uint64_t size, int lane) {
+    if (lane == 0) st_relaxed(&f1[c], kFlagAgg | size);
+}
+
+// Resolves the exclusive prefix of chunk c, whose size was already published.
 __device__ __forceinline__ uint64_t lookback(unsigned long long *f1, unsigned long long *f2, uint64_t c,
                                              uint64_t nchunks, uint64_t size, int lane, Control *ctl,
                                              bool &ok) {
@@ -387,7 +392,6 @@ __device__ __forceinline__ uint64_t lookback(unsigned long long *f1, unsigned lo
     const uint32_t i = (uint32_t)(c & 31u);
     const uint64_t gbeg = q << 5;
     const bool last_in_group = (i == 31u) || (c + 1 == nchunks);
-    if (lane == 0) st_relaxed(&f1[c], kFlagAgg | size);
     uint64_t within = 0, gpref = 0;
     bool within_done = (i == 0), group_done = (q == 0), agg2_sent = false;
     int64_t gtop = (int64_t)q - 1;
