@@ -20,33 +20,53 @@ namespace falcon {
 
 namespace {
 
-constexpr int kBuf = 8256;                  // one chunk of values / one record
+constexpr int kBuf = 8288;                  // one chunk of values / one record (+32 readable)
 constexpr int kScratch = 128;
 constexpr int kWarpBytes = 2 * kBuf + kScratch;
 constexpr int kPlOff = 48;                  // plane words: kPlOff + (W-1-p)*128 + 4*lane
 
-// Moves len bytes from src to dst (byte offsets in the warp buffer, dst <= src) with
-// aligned 32-bit stores.  Bytes before dst in its first word are preserved; the bytes after
-// dst + len in the last word are overwritten (the caller keeps >= 4 free bytes there).
-// Reads run ahead of writes in every iteration, so the overlap dst < src is safe.
+// Copies len bytes from src to dst inside a warp buffer, dst + 14 <= src (the move goes
+// down): unaligned head and tail bytes singly, the 16-byte aligned middle of the
+// destination with one 16-byte store per lane and iteration, its source taken from two
+// aligned 16-byte loads and funnel shifts.  In every iteration all lanes read before any
+// lane writes, and later iterations read strictly above earlier writes, so the overlapping
+// move is safe.  The buffer has 32 readable bytes past any source byte.
+__device__ __forceinline__ uint32_t fsr(uint32_t lo, uint32_t hi, uint32_t s) { return __funnelshift_r(lo, hi, s); }
+
 __device__ __forceinline__ void smem_move_down(uint8_t *buf, uint32_t dst, uint32_t src, uint32_t len, int lane) {
-    const uint32_t d0 = dst & ~3u;
-    const uint32_t head = dst & 3u;
-    const uint32_t nwords = (head + len + 3u) >> 2;
-    const uint32_t shift = src - dst;
-    for (uint32_t j = lane; j < nwords; j += 32) {
-        const uint32_t a = d0 + 4u * j;
-        const uint32_t sa = a + shift;                  // source byte of this word's byte 0
-        const uint32_t s = sa & 3u;
-        const uint32_t *w = reinterpret_cast<const uint32_t *>(buf + (sa - s));
-        uint32_t word = __funnelshift_r(w[0], w[1], 8u * s);
-        if (j == 0 && head) {
-            const uint32_t keep = (1u << (8u * head)) - 1u;
-            word = (word & ~keep) | (*reinterpret_cast<const uint32_t *>(buf + a) & keep);
+    const uint32_t head = min((16u - (dst & 15u)) & 15u, len);
+    uint32_t hb = 0;
+    if ((uint32_t)lane < head) hb = buf[src + lane];
+    __syncwarp();
+    if ((uint32_t)lane < head) buf[dst + lane] = (uint8_t)hb;
+    __syncwarp();
+    const uint32_t D = dst + head, S = src + head;
+    const uint32_t units = (len - head) >> 4;
+    const uint32_t off = S & 15u, k0 = off >> 2, sb = (off & 3u) * 8u;
+    const uint32_t Sa = S - off;
+    for (uint32_t u0 = 0; u0 < units; u0 += 32) {
+        const uint32_t u = u0 + lane;
+        uint4 o = make_uint4(0, 0, 0, 0);
+        if (u < units) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(buf + Sa + 16u * u);
+            const uint4 b = *reinterpret_cast<const uint4 *>(buf + Sa + 16u * u + 16u);
+            switch (k0) {
+                case 0: o = make_uint4(fsr(a.x, a.y, sb), fsr(a.y, a.z, sb), fsr(a.z, a.w, sb), fsr(a.w, b.x, sb)); break;
+                case 1: o = make_uint4(fsr(a.y, a.z, sb), fsr(a.z, a.w, sb), fsr(a.w, b.x, sb), fsr(b.x, b.y, sb)); break;
+                case 2: o = make_uint4(fsr(a.z, a.w, sb), fsr(a.w, b.x, sb), fsr(b.x, b.y, sb), fsr(b.y, b.z, sb)); break;
+                default: o = make_uint4(fsr(a.w, b.x, sb), fsr(b.x, b.y, sb), fsr(b.y, b.z, sb), fsr(b.z, b.w, sb)); break;
+            }
         }
-        __syncwarp(__activemask());
-        *reinterpret_cast<uint32_t *>(buf + a) = word;
+        __syncwarp();
+        if (u < units) *reinterpret_cast<uint4 *>(buf + D + 16u * u) = o;
     }
+    __syncwarp();
+    const uint32_t tail = (len - head) & 15u;
+    const uint32_t T0 = units * 16u;
+    uint32_t tb = 0;
+    if ((uint32_t)lane < tail) tb = buf[S + T0 + lane];
+    __syncwarp();
+    if ((uint32_t)lane < tail) buf[D + T0 + lane] = (uint8_t)tb;
     __syncwarp();
 }
 
@@ -184,16 +204,42 @@ __device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t 
     read_own<F64>(buf, lane, m, v);
     U vx = 0;                                   // value 1024 of a 1025-value chunk
     if (m > 1024u && lane == 31) vx = read_elem<F64>(buf, 1024);
-    bool sp = is_special(vx);
-    U vmax = vx & ABS;
+    bool sp;
+    U vmax;
+    if constexpr (F64) {
+        // on 32-bit halves: special <=> exponent field all zeros (value != +0) or all ones
+        uint32_t hmax = 0;
+        bool s = false;
+        auto cls = [&](uint64_t u) {
+            const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u, ha = hi & 0x7FFFFFFFu;
+            s |= (ha - 0x00100000u >= 0x7FE00000u) && ((hi | lo) != 0u);
+            hmax = ha > hmax ? ha : hmax;
+        };
+        cls(vx);
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        sp |= is_special(v[k]);
-        const U a = v[k] & ABS;
-        vmax = a > vmax ? a : vmax;
+        for (int k = 0; k < 32; ++k) cls(v[k]);
+        sp = __any_sync(kFull, s);
+        const uint32_t H = __reduce_max_sync(kFull, hmax);
+        uint32_t lmax = 0;
+        auto lo_of = [&](uint64_t u) {
+            if (((uint32_t)(u >> 32) & 0x7FFFFFFFu) == H) lmax = (uint32_t)u > lmax ? (uint32_t)u : lmax;
+        };
+        lo_of(vx);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) lo_of(v[k]);
+        vmax = ((uint64_t)H << 32) | __reduce_max_sync(kFull, lmax);
+    } else {
+        sp = is_special(vx);
+        vmax = vx & ABS;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            sp |= is_special(v[k]);
+            const U a = v[k] & ABS;
+            vmax = a > vmax ? a : vmax;
+        }
+        sp = __any_sync(kFull, sp);
+        vmax = warp_max_x(vmax);
     }
-    sp = __any_sync(kFull, sp);
-    vmax = warp_max_x(vmax);
 
     // ---- 2. Case decision (Eq. 4) -----------------------------------------------------------
     int alpha = -1;                             // -1: Case 2
@@ -268,7 +314,7 @@ __device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t 
     const uint32_t cols = chunk_cols(m);
     const uint32_t nact = cols / 32u;            // lanes holding row bytes
     const uint32_t row_bytes = cols / 8u;
-    const bool active = (uint32_t)lane < nact;
+    // lanes past the row (lane >= nact) hold only pad columns, i.e. zero plane words
     uint32_t packed[T::W / 4];
     {
         uint32_t a[32];
@@ -278,7 +324,7 @@ __device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t 
 #pragma unroll
         for (int p = 0; p < 32; ++p) {
             *reinterpret_cast<uint32_t *>(buf + kPlOff + (T::W - 1 - p) * 128 + 4 * lane) = a[p];
-            const uint32_t nzb = active ? (uint32_t)__popc((((a[p] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | a[p]) & 0x80808080u) : 0u;
+            const uint32_t nzb = (uint32_t)__popc((((a[p] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | a[p]) & 0x80808080u);
             if (p % 4 == 0) packed[p / 4] = nzb;
             else packed[p / 4] |= nzb << (8 * (p % 4));
         }
@@ -292,7 +338,7 @@ __device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t 
 #pragma unroll
             for (int p = 0; p < 32; ++p) {
                 *reinterpret_cast<uint32_t *>(buf + kPlOff + (31 - p) * 128 + 4 * lane) = a[p];
-                const uint32_t nzb = active ? (uint32_t)__popc((((a[p] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | a[p]) & 0x80808080u) : 0u;
+                const uint32_t nzb = (uint32_t)__popc((((a[p] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | a[p]) & 0x80808080u);
                 if (p % 4 == 0) packed[8 + p / 4] = nzb;
                 else packed[8 + p / 4] |= nzb << (8 * (p % 4));
             }
@@ -395,17 +441,16 @@ __device__ bool finish_chunk(const Job &job, const Pend &pd, uint8_t *buf, int l
     while (p >= 0) {
         const uint32_t src = kPlOff + (uint32_t)(T::W - 1 - p) * 128u;
         if ((dense_mask >> p) & 1ull) {
-            // a run of dense rows p, p-1, ... : contiguous in the plane buffer when rows are
-            // 128 bytes long, so one shifted move copies the whole run
+            // a run of dense rows p, p-1, ..., q: contiguous in the plane buffer when rows
+            // are 128 bytes long, so one move copies the whole run
             int q = p;
-            if (row_bytes == 128u)
-                while (q > 0 && ((dense_mask >> (q - 1)) & 1ull)) --q;
-            const uint32_t rows = (uint32_t)(p - q + 1);
             if (row_bytes == 128u) {
-                smem_move_down(buf, pos, src, rows * 128u, lane);
-            } else {
-                smem_move_down(buf, pos, src, row_bytes, lane);
+                const uint64_t below = (p >= 63) ? ~0ull : ((2ull << p) - 1ull);
+                const uint64_t holes = ~dense_mask & below;               // sparse rows <= p
+                q = holes ? 64 - __clzll((long long)holes) : 0;           // lowest row of the run
             }
+            const uint32_t rows = (uint32_t)(p - q + 1);
+            smem_move_down(buf, pos, src, rows * row_bytes, lane);
             pos += rows * row_bytes;
             p = q - 1;
         } else {
@@ -449,6 +494,9 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
     const int warp = threadIdx.x >> 5;
     uint8_t *wbase = smem + warp * kWarpBytes;
     uint8_t *scratch = wbase + 2 * kBuf;
+    __shared__ Job s_single;                      // the single job, read from shared memory
+    if (threadIdx.x == 0) s_single = single;
+    __syncthreads();
 
     // jobs without chunks (n = 0) still get a header and a length
     {
@@ -456,7 +504,7 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
         const int nw = gridDim.x * kWarpsPerCta;
         const int nj = (jobs != nullptr) ? njobs : 1;
         for (int j = gw; j < nj; j += nw) {
-            const Job &jb = (jobs != nullptr) ? jobs[j] : single;
+            const Job &jb = (jobs != nullptr) ? jobs[j] : s_single;
             if (jb.nchunks == 0 && lane == 0) {
                 uint4 *dst = reinterpret_cast<uint4 *>(jb.out);
                 if (jb.out_cap >= 32) {
@@ -482,9 +530,9 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
         t = shfl_u64(t, 0);
         if (t >= total_chunks) break;
         if (*reinterpret_cast<volatile unsigned int *>(&ctl->abort)) break;
-        const Job &job = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
+        const Job &job = (jobs == nullptr) ? s_single : jobs[find_job(jobs, njobs, t)];
         uint8_t *buf = wbase + cur * kBuf;
-        issue_chunk(jobs, njobs, single, t, buf, lane);
+        issue_chunk(jobs, njobs, s_single, t, buf, lane);
         cp_async_commit();
         cp_async_wait_none();
         __syncwarp();
@@ -492,7 +540,7 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
         if (job.dtype == 0) compute_chunk<true>(job, t, buf, scratch, lane, hint64, next);
         else compute_chunk<false>(job, t, buf, scratch, lane, hint32, next);
         if (pend.valid) {
-            const Job &pj = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, pend.t)];
+            const Job &pj = (jobs == nullptr) ? s_single : jobs[find_job(jobs, njobs, pend.t)];
             const bool ok = (pj.dtype == 0) ? finish_chunk<true>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl)
                                             : finish_chunk<false>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl);
             if (!ok) return;
@@ -501,7 +549,7 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
         cur ^= 1;
     }
     if (pend.valid) {
-        const Job &pj = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, pend.t)];
+        const Job &pj = (jobs == nullptr) ? s_single : jobs[find_job(jobs, njobs, pend.t)];
         if (pj.dtype == 0) finish_chunk<true>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl);
         else finish_chunk<false>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl);
     }

@@ -124,80 +124,102 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     }
     const bool active = (uint32_t)lane < nact;
     const uint32_t bm_bytes = nact / 2u;
+    const uint32_t hdr = pos;
+    const uint64_t wmask = (w >= 64u) ? ~0ull : ((1ull << w) - 1ull);
+    // Sparse rows only (top to bottom): a sparse row's position is the header, the dense rows
+    // above it (row_bytes each) and the sparse rows above it.  Dense rows need no walk.
+    uint64_t sparse = bad ? 0ull : (~dense_mask & wmask);
+    uint32_t sparse_sum = 0, deficit = 0;
 #pragma unroll 1
-    for (int p = (int)w - 1; p >= 0 && !bad; --p) {
-        if (lane == 0) rowpos[p] = (uint16_t)pos;
-        if ((dense_mask >> p) & 1ull) {
-            pos += row_bytes;
-            if (pos > size) bad = true;
-        } else {
-            if (pos + bm_bytes > size) { bad = true; break; }
-            uint32_t nib = 0;
-            if (active) {
-                const uint32_t byte = rec[pos + (lane >> 1)];
-                nib = (lane & 1) ? (byte & 0xFu) : (byte >> 4);
-            }
-            const uint32_t cnt = __popc(nib);
-            const unsigned b0 = __ballot_sync(kFull, cnt & 1u);
-            const unsigned b1 = __ballot_sync(kFull, cnt & 2u);
-            const unsigned b2 = __ballot_sync(kFull, cnt & 4u);
-            const unsigned lt = (1u << lane) - 1u;
-            const uint32_t before = __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt);
-            const uint32_t nnz = __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2);
-            if (pos + bm_bytes + nnz > size) { bad = true; break; }
-            uint32_t x = 0, q = pos + bm_bytes + before;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if ((nib >> (3 - i)) & 1u) x |= (uint32_t)rec[q++] << (8 * i);
-            *reinterpret_cast<uint32_t *>(pbuf + p * 128 + 4 * lane) = x;
-            pos += bm_bytes + nnz;
+    while (sparse && !bad) {
+        const int p = 63 - __clzll((long long)sparse);
+        sparse &= ~(1ull << p);
+        const uint64_t above = (p >= 63) ? 0ull : (wmask & ~((2ull << p) - 1ull));
+        const uint32_t spos = hdr + row_bytes * (uint32_t)__popcll(dense_mask & above) + sparse_sum;
+        if (spos + bm_bytes > size) { bad = true; break; }
+        uint32_t nib = 0;
+        if (active) {
+            const uint32_t byte = rec[spos + (lane >> 1)];
+            nib = (lane & 1) ? (byte & 0xFu) : (byte >> 4);
         }
+        const uint32_t cnt = __popc(nib);
+        const unsigned b0 = __ballot_sync(kFull, cnt & 1u);
+        const unsigned b1 = __ballot_sync(kFull, cnt & 2u);
+        const unsigned b2 = __ballot_sync(kFull, cnt & 4u);
+        const unsigned lt = (1u << lane) - 1u;
+        const uint32_t before = __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt);
+        const uint32_t nnz = __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2);
+        if (spos + bm_bytes + nnz > size) { bad = true; break; }
+        uint32_t x = 0, q = spos + bm_bytes + before;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if ((nib >> (3 - i)) & 1u) x |= (uint32_t)rec[q++] << (8 * i);
+        *reinterpret_cast<uint32_t *>(pbuf + p * 128 + 4 * lane) = x;
+        sparse_sum += bm_bytes + nnz;
+        if (lane == 0) rowpos[p] = (uint16_t)(row_bytes - (bm_bytes + nnz));   // bytes saved
+        deficit += row_bytes - (bm_bytes + nnz);
     }
-    if (pos != size) bad = true;
+    if (!bad && hdr + row_bytes * (uint32_t)__popcll(dense_mask & wmask) + sparse_sum != size) bad = true;
     if (bad) {
         if (lane == 0) set_status(job.result, kErrCorrupt);
         return;
     }
+    (void)deficit;
     __syncwarp();
 
     // ---- b. gather plane words, Z -> G -> values ------------------------------------------
+    // dense row p sits at hdr + row_bytes * (w-1-p) - (bytes saved by the sparse rows above p)
     U d[32];
+    uint32_t saved = 0;                          // running over p = w-1 .. 0
+    if constexpr (F64) {
+        if (w > 32) {
+            uint32_t a[32];
+#pragma unroll
+            for (int i = 31; i >= 0; --i) {
+                const int p = i + 32;
+                uint32_t x = 0;
+                if ((uint32_t)p < w) {
+                    if ((dense_mask >> p) & 1ull) {
+                        const uint32_t rp = hdr + row_bytes * (w - 1u - (uint32_t)p) - saved;
+                        if (active) x = ld_u32_unaligned(rbuf, sh + rp + 4u * lane);
+                    } else {
+                        x = *reinterpret_cast<const uint32_t *>(pbuf + p * 128 + 4 * lane);
+                        saved += rowpos[p];
+                    }
+                }
+                a[i] = x;
+            }
+            transpose32(a);
+#pragma unroll
+            for (int k = 0; k < 32; ++k) d[k] = (U)a[k ^ 7] << 32;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) d[k] = 0;
+        }
+    }
     {
         uint32_t a[32];
 #pragma unroll
-        for (int p = 0; p < 32; ++p) {
+        for (int p = 31; p >= 0; --p) {
             uint32_t x = 0;
             if ((uint32_t)p < w) {
                 if ((dense_mask >> p) & 1ull) {
-                    if (active) x = ld_u32_unaligned(rbuf, sh + rowpos[p] + 4u * lane);
+                    const uint32_t rp = hdr + row_bytes * (w - 1u - (uint32_t)p) - saved;
+                    if (active) x = ld_u32_unaligned(rbuf, sh + rp + 4u * lane);
                 } else {
                     x = *reinterpret_cast<const uint32_t *>(pbuf + p * 128 + 4 * lane);
+                    saved += rowpos[p];
                 }
             }
             a[p] = x;
         }
         transpose32(a);
+        if constexpr (F64) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) d[k] = (U)a[k ^ 7];
-    }
-    if constexpr (F64) {
-        if (w > 32) {
-            uint32_t a[32];
+            for (int k = 0; k < 32; ++k) d[k] |= (U)a[k ^ 7];
+        } else {
 #pragma unroll
-            for (int p = 0; p < 32; ++p) {
-                uint32_t x = 0;
-                if ((uint32_t)(p + 32) < w) {
-                    if ((dense_mask >> (p + 32)) & 1ull) {
-                        if (active) x = ld_u32_unaligned(rbuf, sh + rowpos[p + 32] + 4u * lane);
-                    } else {
-                        x = *reinterpret_cast<const uint32_t *>(pbuf + (p + 32) * 128 + 4 * lane);
-                    }
-                }
-                a[p] = x;
-            }
-            transpose32(a);
-#pragma unroll
-            for (int k = 0; k < 32; ++k) d[k] |= (U)a[k ^ 7] << 32;
+            for (int k = 0; k < 32; ++k) d[k] = (U)a[k ^ 7];
         }
     }
     U run = 0;
@@ -323,32 +345,35 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
     const int warp = threadIdx.x >> 5;
     uint8_t *wbase = smem + warp * kWarpBytes;
     uint8_t *pbuf = wbase + 2 * kBuf;
+    __shared__ Job s_single;                      // the single job, read from shared memory
+    if (threadIdx.x == 0) s_single = single;
+    __syncthreads();
     const uint64_t gw = (uint64_t)blockIdx.x * kWarpsPerCta + warp;
     const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
     (void)ctl;
     for (uint64_t j = gw; j < (uint64_t)((jobs != nullptr) ? njobs : 1); j += nw) {
-        const Job &jb = (jobs != nullptr) ? jobs[j] : single;
+        const Job &jb = (jobs != nullptr) ? jobs[j] : s_single;
         if (lane == 0) jb.result[0] = jb.n;
     }
     if (gw >= total_chunks) return;
     int cur = 0;
-    Loc lc = locate(jobs, njobs, single, gw);
-    bool okc = issue_record(job_of(jobs, njobs, single, gw), lc, wbase, lane);
+    Loc lc = locate(jobs, njobs, s_single, gw);
+    bool okc = issue_record(job_of(jobs, njobs, s_single, gw), lc, wbase, lane);
     cp_async_commit();
     Loc ln{};
-    if (gw + nw < total_chunks) ln = locate(jobs, njobs, single, gw + nw);
+    if (gw + nw < total_chunks) ln = locate(jobs, njobs, s_single, gw + nw);
     for (uint64_t t = gw; t < total_chunks; t += nw) {
         const uint64_t tn = t + nw;
         bool okn = false;
         Loc lnn{};
         if (tn < total_chunks) {
-            okn = issue_record(job_of(jobs, njobs, single, tn), ln, wbase + (cur ^ 1) * kBuf, lane);
-            if (tn + nw < total_chunks) lnn = locate(jobs, njobs, single, tn + nw);
+            okn = issue_record(job_of(jobs, njobs, s_single, tn), ln, wbase + (cur ^ 1) * kBuf, lane);
+            if (tn + nw < total_chunks) lnn = locate(jobs, njobs, s_single, tn + nw);
         }
         cp_async_commit();
         cp_async_wait_prior();                   // the current record has landed
         __syncwarp();
-        const Job &job = job_of(jobs, njobs, single, t);
+        const Job &job = job_of(jobs, njobs, s_single, t);
         if (job.dtype == 0) decode_chunk<true>(job, lc, okc, wbase + cur * kBuf, pbuf, lane);
         else decode_chunk<false>(job, lc, okc, wbase + cur * kBuf, pbuf, lane);
         lc = ln;

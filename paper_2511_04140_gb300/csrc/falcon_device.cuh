@@ -144,6 +144,21 @@ __device__ __forceinline__ uint32_t nonzero_nibble(uint32_t x) {
 // Recursive exchange of the off-diagonal blocks (Hacker's Delight, Sec. 7-3).
 // --------------------------------------------------------------------------------------
 __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
+    // 16- and 8-bit block exchanges are byte permutations (one PRMT per output word)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const uint32_t x = a[k], y = a[k + 16];
+        a[k] = __byte_perm(x, y, 0x5410);
+        a[k + 16] = __byte_perm(x, y, 0x7632);
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        if ((k & 8) == 0) {
+            const uint32_t x = a[k], y = a[k + 8];
+            a[k] = __byte_perm(x, y, 0x6240);
+            a[k + 8] = __byte_perm(x, y, 0x7351);
+        }
+    }
 #define FALCON_TSTEP(h, mask)                                                       \
     _Pragma("unroll") for (int k = 0; k < 32; ++k) {                               \
         if ((k & (h)) == 0) {                                                       \
@@ -152,8 +167,6 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
             a[k] ^= t << (h);                                                       \
         }                                                                           \
     }
-    FALCON_TSTEP(16, 0x0000FFFFu)
-    FALCON_TSTEP(8, 0x00FF00FFu)
     FALCON_TSTEP(4, 0x0F0F0F0Fu)
     FALCON_TSTEP(2, 0x33333333u)
     FALCON_TSTEP(1, 0x55555555u)
@@ -187,7 +200,18 @@ __device__ __forceinline__ void stage_values_async(const uint8_t *src, uint32_t 
     uint32_t done = 0;
     if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
         const uint32_t nunits = nbytes >> 4;
-        for (uint32_t q = lane; q < nunits; q += 32) cp_async16(base + phys_unit<F64>(q) * 16u, src + 16u * q);
+        constexpr uint32_t FULL_UNITS = 1024u * S / 16u;    // a whole 1024-value chunk
+        if (nunits >= FULL_UNITS) {
+            // unit q = lane + 32 i belongs to lane L = q / UNITS, slot u = q % UNITS
+#pragma unroll
+            for (uint32_t i = 0; i < FULL_UNITS / 32u; ++i) {
+                const uint32_t q = lane + 32u * i;
+                cp_async16(base + phys_unit<F64>(q) * 16u, src + 16u * q);
+            }
+            for (uint32_t q = FULL_UNITS + lane; q < nunits; q += 32) cp_async16(base + phys_unit<F64>(q) * 16u, src + 16u * q);
+        } else {
+            for (uint32_t q = lane; q < nunits; q += 32) cp_async16(base + phys_unit<F64>(q) * 16u, src + 16u * q);
+        }
         done = (nunits * 16u) / S;
     }
     for (uint32_t e = done + lane; e < m; e += 32) {
@@ -216,9 +240,11 @@ __device__ __forceinline__ void read_own(const uint8_t *wsm, int lane, uint32_t 
             v[PER * u + 3] = q.w;
         }
     }
+    if (m < 1024u) {                              // a tail chunk: values past m read as +0
 #pragma unroll
-    for (int k = 0; k < 32; ++k)
-        if ((uint32_t)(32 * lane + k) >= m) v[k] = 0;
+        for (int k = 0; k < 32; ++k)
+            if ((uint32_t)(32 * lane + k) >= m) v[k] = 0;
+    }
 }
 
 template <bool F64>
