@@ -119,6 +119,50 @@ int falcon_decompress_async(const void *d_in, size_t in_bytes, const void *h_hea
 /* Frees the workspaces cached by falcon_compress / falcon_decompress on every device. */
 int falcon_release(void);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched form: many independent series (mixed lengths, dtypes and block sizes) compressed
+ * or decompressed by ONE persistent kernel launch over all (series, chunk) work items
+ * (decompression adds one small offsets launch).  Each series still produces / consumes
+ * its own self-describing stream.  The paper processes one batch per kernel call (Alg. 1,
+ * Alg. 3); this entry point is how the library serves many series at once.
+ * ------------------------------------------------------------------------------------- */
+typedef enum { FALCON_COMPRESS = 0, FALCON_DECOMPRESS = 1 } falcon_direction;
+
+typedef struct {
+    const void *d_in;       /* compress: n values (device); decompress: a stream (device) */
+    void *d_out;            /* compress: stream buffer; decompress: value buffer (device) */
+    uint64_t n;             /* compress: number of values (decompress: taken from h_header) */
+    uint64_t in_bytes;      /* decompress: stream length in bytes (compress: ignored) */
+    uint64_t out_capacity;  /* bytes available at d_out */
+    int32_t dtype;          /* compress: FALCON_F64 or FALCON_F32 (decompress: ignored) */
+    uint32_t block_size;    /* compress: values per chunk (decompress: ignored) */
+    const void *h_header;   /* decompress: HOST copy of the stream's first 32 bytes; compress: NULL */
+} falcon_series;
+
+/* Device workspace (bytes) a batch plan of `count` series needs (job table + look-back
+ * words).  Returns 0 if a series is invalid. */
+size_t falcon_batch_workspace_bytes(int direction, const falcon_series *h_series, int count);
+
+/* Validates the series, lays out the job table and look-back words in d_workspace (256-byte
+ * aligned device memory of workspace_bytes) and uploads the table with a copy enqueued on
+ * `stream`.  d_results (device, 2 * count uint64): after each launch [2i] = stream bytes
+ * (compress) or values (decompress) of series i and [2i+1] = its falcon_status.
+ * The plan stays valid until falcon_batch_forget(d_workspace) or a new plan on the same
+ * workspace; buffers named in it must stay allocated while it is launched. */
+int falcon_batch_plan(int direction, const falcon_series *h_series, int count, void *d_workspace,
+                      size_t workspace_bytes, uint64_t *d_results, void *stream);
+
+/* Enqueues one execution of the plan held by d_workspace on `stream` (workspace and result
+ * reset, then the persistent kernel): no host synchronisation, capturable in a CUDA graph. */
+int falcon_batch_launch(void *d_workspace, void *stream);
+
+/* Drops the host-side record of the plan held by d_workspace. */
+int falcon_batch_forget(void *d_workspace);
+
+/* Persistent-grid size: at most ctas_per_sm resident CTAs per SM for each direction
+ * (0 = as many as fit).  Does not change any output byte; used by the autotuner. */
+int falcon_set_launch_config(int compress_ctas_per_sm, int decompress_ctas_per_sm);
+
 #ifdef __cplusplus
 }
 #endif

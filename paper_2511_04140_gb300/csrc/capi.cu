@@ -3,11 +3,16 @@
 #include <cstring>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "falcon.h"
 #include "falcon_internal.h"
 
 using namespace falcon;
+
+namespace falcon {
+int g_ctas_per_sm[2] = {0, 0};
+}
 
 namespace {
 
@@ -296,6 +301,140 @@ int falcon_release(void) {
     }
     g_ws.clear();
     cudaSetDevice(cur);
+    return FALCON_OK;
+}
+
+}  // extern "C"
+
+/* ------------------------------------------------------------------------- batched form */
+
+namespace {
+struct BatchPlan {
+    int direction;
+    int count;
+    uint64_t total_chunks;
+    size_t reset_bytes;       // control block + look-back words, zeroed before each launch
+    uint64_t *d_results;
+};
+std::mutex g_plan_mu;
+std::unordered_map<uintptr_t, BatchPlan> g_plans;
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Host-side job table for a batch (no device pointers dereferenced); returns a status.
+int build_jobs(int direction, const falcon_series *series, int count, std::vector<Job> &jobs,
+               uint64_t &total_chunks, size_t &words) {
+    jobs.resize((size_t)count);
+    total_chunks = 0;
+    words = 0;
+    for (int i = 0; i < count; ++i) {
+        const falcon_series &sr = series[i];
+        Job j{};
+        if (direction == FALCON_COMPRESS) {
+            const int st = compress_args(sr.d_in, sr.n, sr.dtype, sr.block_size, sr.d_out, sr.out_capacity);
+            if (st) return st;
+            j = make_compress_job(sr.d_in, sr.n, sr.dtype, sr.block_size, sr.d_out, sr.out_capacity, nullptr, nullptr);
+        } else if (direction == FALCON_DECOMPRESS) {
+            if (!sr.h_header || !sr.d_in) return FALCON_ERR_INVALID;
+            if ((uintptr_t)sr.d_in % 16 != 0) return FALCON_ERR_INVALID;
+            if (sr.in_bytes < FALCON_HEADER_BYTES) return FALCON_ERR_CORRUPT;
+            Header h;
+            int st = parse_header(static_cast<const uint8_t *>(sr.h_header), FALCON_HEADER_BYTES, &h);
+            if (st) return st;
+            if ((st = decompress_args(sr.d_in, sr.in_bytes, h, sr.d_out, sr.out_capacity))) return st;
+            j = make_decompress_job(sr.d_in, sr.in_bytes, h, sr.d_out, sr.out_capacity, nullptr, nullptr);
+        } else {
+            return FALCON_ERR_INVALID;
+        }
+        j.chunk_begin = total_chunks;
+        total_chunks += j.nchunks;
+        // look-back words (compress) / chunk offsets (decompress), 8-byte each
+        j.flags = reinterpret_cast<unsigned long long *>((uintptr_t)words);   // offset, fixed up later
+        words += (size_t)(j.nchunks + (j.nchunks + 31) / 32);
+        jobs[(size_t)i] = j;
+    }
+    return FALCON_OK;
+}
+}  // namespace
+
+extern "C" {
+
+size_t falcon_batch_workspace_bytes(int direction, const falcon_series *h_series, int count) {
+    if (count < 0 || (count > 0 && !h_series)) return 0;
+    std::vector<Job> jobs;
+    uint64_t total = 0;
+    size_t words = 0;
+    if (build_jobs(direction, h_series, count, jobs, total, words) != FALCON_OK) return 0;
+    return kControlBytes + align256(sizeof(Job) * (size_t)count) + align256(8 * words);
+}
+
+int falcon_batch_plan(int direction, const falcon_series *h_series, int count, void *d_workspace,
+                      size_t workspace_bytes, uint64_t *d_results, void *stream) {
+    if (count < 0 || (count > 0 && (!h_series || !d_results)) || !d_workspace) return FALCON_ERR_INVALID;
+    if ((uintptr_t)d_workspace % 256 != 0 || (uintptr_t)d_results % 8 != 0) return FALCON_ERR_INVALID;
+    std::vector<Job> jobs;
+    uint64_t total = 0;
+    size_t words = 0;
+    int st = build_jobs(direction, h_series, count, jobs, total, words);
+    if (st) return st;
+    const size_t table = align256(sizeof(Job) * (size_t)count);
+    const size_t need = kControlBytes + table + align256(8 * words);
+    if (workspace_bytes < need) return FALCON_ERR_INVALID;
+    uint8_t *w8 = static_cast<uint8_t *>(d_workspace);
+    unsigned long long *flags = reinterpret_cast<unsigned long long *>(w8 + kControlBytes + table);
+    for (int i = 0; i < count; ++i) {
+        jobs[(size_t)i].flags = flags + (uintptr_t)jobs[(size_t)i].flags;
+        jobs[(size_t)i].result = reinterpret_cast<unsigned long long *>(d_results + 2 * (size_t)i);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (count > 0 &&
+        cudaMemcpyAsync(w8 + kControlBytes, jobs.data(), sizeof(Job) * (size_t)count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return FALCON_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FALCON_ERR_CUDA;   // the host table is freed below
+    BatchPlan plan{direction, count, total, kControlBytes + table + 8 * words, d_results};
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans[(uintptr_t)d_workspace] = plan;
+    return FALCON_OK;
+}
+
+int falcon_batch_launch(void *d_workspace, void *stream) {
+    BatchPlan plan;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        auto it = g_plans.find((uintptr_t)d_workspace);
+        if (it == g_plans.end()) return FALCON_ERR_INVALID;
+        plan = it->second;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t *w8 = static_cast<uint8_t *>(d_workspace);
+    // the control block and the look-back words; the job table in between is kept
+    const size_t table = align256(sizeof(Job) * (size_t)plan.count);
+    if (cudaMemsetAsync(w8, 0, kControlBytes, s) != cudaSuccess) return FALCON_ERR_CUDA;
+    if (plan.reset_bytes > kControlBytes + table &&
+        cudaMemsetAsync(w8 + kControlBytes + table, 0, plan.reset_bytes - kControlBytes - table, s) != cudaSuccess)
+        return FALCON_ERR_CUDA;
+    if (plan.count > 0 && cudaMemsetAsync(plan.d_results, 0, 16 * (size_t)plan.count, s) != cudaSuccess)
+        return FALCON_ERR_CUDA;
+    if (plan.count == 0) return FALCON_OK;
+    const Job *d_jobs = reinterpret_cast<const Job *>(w8 + kControlBytes);
+    Control *ctl = reinterpret_cast<Control *>(w8);
+    Job dummy{};
+    const cudaError_t e = (plan.direction == FALCON_COMPRESS)
+                              ? launch_compress(d_jobs, plan.count, dummy, plan.total_chunks, ctl, s)
+                              : launch_decompress(d_jobs, plan.count, dummy, plan.total_chunks, ctl, s);
+    return e == cudaSuccess ? FALCON_OK : FALCON_ERR_CUDA;
+}
+
+int falcon_batch_forget(void *d_workspace) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans.erase((uintptr_t)d_workspace);
+    return FALCON_OK;
+}
+
+int falcon_set_launch_config(int compress_ctas_per_sm, int decompress_ctas_per_sm) {
+    if (compress_ctas_per_sm < 0 || decompress_ctas_per_sm < 0) return FALCON_ERR_INVALID;
+    g_ctas_per_sm[0] = compress_ctas_per_sm;
+    g_ctas_per_sm[1] = decompress_ctas_per_sm;
     return FALCON_OK;
 }
 

@@ -557,19 +557,23 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
 
 constexpr int kCompressCtaSmem = kWarpsPerCta * kWarpBytes;
 
-static int g_grid_cache[64] = {0};
+static int g_occ_cache[64] = {0};
+static int g_sms_cache[64] = {0};
 
 int compress_grid(uint64_t total_chunks) {
     int dev = 0;
     cudaGetDevice(&dev);
-    int &cached = g_grid_cache[dev & 63];
-    if (cached == 0) {
+    int &occ_c = g_occ_cache[dev & 63];
+    if (occ_c == 0) {
         cudaFuncSetAttribute(compress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCompressCtaSmem);
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, compress_kernel, kThreads, kCompressCtaSmem);
-        cached = sms * (occ > 0 ? occ : 1);
+        g_sms_cache[dev & 63] = sms;
+        occ_c = occ > 0 ? occ : 1;
     }
+    const int lim = g_ctas_per_sm[0];
+    const int cached = g_sms_cache[dev & 63] * ((lim > 0 && lim < occ_c) ? lim : occ_c);
     const uint64_t need = (total_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
     return (int)(need < (uint64_t)cached ? (need > 0 ? need : 1) : (uint64_t)cached);
 }

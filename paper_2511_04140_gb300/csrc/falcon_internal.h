@@ -49,6 +49,10 @@ cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single,
 cudaError_t launch_decompress(const Job *d_jobs, int njobs, const Job &single,
                               uint64_t total_chunks, Control *ctl, cudaStream_t stream);
 
+// Resident CTAs per SM used by the persistent grids (0 = occupancy limit); [0] compress,
+// [1] decompress.  Set through falcon_set_launch_config.
+extern int g_ctas_per_sm[2];
+
 // Grid size used for a launch over total_chunks work items (persistent, occupancy-bound).
 int compress_grid(uint64_t total_chunks);
 int decompress_grid(uint64_t total_chunks);

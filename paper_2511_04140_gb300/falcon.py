@@ -22,6 +22,14 @@ MAX_BLOCK = 1025
 
 _lock = threading.Lock()
 _lib = None
+COMPRESS, DECOMPRESS = 0, 1
+
+
+class Series(ctypes.Structure):
+    """falcon_series (include/falcon.h)."""
+    _fields_ = [("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("in_bytes", ctypes.c_uint64), ("out_capacity", ctypes.c_uint64), ("dtype", ctypes.c_int32),
+                ("block_size", ctypes.c_uint32), ("h_header", ctypes.c_void_p)]
 
 
 class FalconError(RuntimeError):
@@ -59,6 +67,16 @@ def _load():
             L.falcon_decompress_async.restype = ci
             L.falcon_decompress_async.argtypes = [vp, sz, vp, vp, sz, vp, sz, vp, vp]
             L.falcon_release.restype = ci
+            L.falcon_batch_workspace_bytes.restype = sz
+            L.falcon_batch_workspace_bytes.argtypes = [ci, c.POINTER(Series), ci]
+            L.falcon_batch_plan.restype = ci
+            L.falcon_batch_plan.argtypes = [ci, c.POINTER(Series), ci, vp, sz, vp, vp]
+            L.falcon_batch_launch.restype = ci
+            L.falcon_batch_launch.argtypes = [vp, vp]
+            L.falcon_batch_forget.restype = ci
+            L.falcon_batch_forget.argtypes = [vp]
+            L.falcon_set_launch_config.restype = ci
+            L.falcon_set_launch_config.argtypes = [ci, ci]
             _lib = L
     return _lib
 
@@ -157,3 +175,81 @@ def decompress_async(s: torch.Tensor, nbytes: int, header: bytes, out: torch.Ten
 
 def release() -> None:
     _load().falcon_release()
+
+
+def set_launch_config(compress_ctas_per_sm: int = 0, decompress_ctas_per_sm: int = 0) -> None:
+    """Caps the persistent grids at the given CTAs per SM (0 = occupancy limit)."""
+    _check(_load().falcon_set_launch_config(compress_ctas_per_sm, decompress_ctas_per_sm), "set_launch_config")
+
+
+class Batch:
+    """A planned batched launch over many series (one persistent kernel per launch).
+
+    compress:   Batch(COMPRESS, inputs=[tensor...], block=1024)       -> outputs: uint8 streams
+    decompress: Batch(DECOMPRESS, inputs=[(stream_tensor, nbytes, header_bytes), ...])
+
+    launch(stream) only enqueues work (capturable in a CUDA graph); results() reads
+    [bytes-or-values, status] per series back to the host.
+    """
+
+    def __init__(self, direction: int, inputs, block: int = 1024, outputs=None, device=None):
+        self.direction = direction
+        self.inputs = list(inputs)
+        n = len(self.inputs)
+        arr = (Series * max(n, 1))()
+        self._headers = []
+        self.outputs = []
+        for i, item in enumerate(self.inputs):
+            sr = arr[i]
+            if direction == COMPRESS:
+                x = item
+                code = _dtype_code(x)
+                cap = bound(x.numel(), code, block)
+                out = outputs[i] if outputs is not None else torch.empty(max(cap, 32), dtype=torch.uint8, device=x.device)
+                sr.d_in, sr.d_out, sr.n = x.data_ptr(), out.data_ptr(), x.numel()
+                sr.out_capacity, sr.dtype, sr.block_size = out.numel(), code, block
+                sr.h_header = None
+            else:
+                s_t, nbytes, hdr = item
+                hb = ctypes.create_string_buffer(bytes(hdr)[:HEADER_BYTES], HEADER_BYTES)
+                self._headers.append(hb)
+                nval, code, _, _ = stream_info(bytes(hdr))
+                dtype = torch.float64 if code == F64 else torch.float32
+                out = outputs[i] if outputs is not None else torch.empty(max(nval, 1), dtype=dtype, device=s_t.device)
+                sr.d_in, sr.d_out, sr.in_bytes = s_t.data_ptr(), out.data_ptr(), nbytes
+                sr.out_capacity = out.numel() * out.element_size()
+                sr.h_header = ctypes.cast(hb, ctypes.c_void_p)
+            self.outputs.append(out)
+        self._series = arr
+        L = _load()
+        ws_bytes = L.falcon_batch_workspace_bytes(direction, arr, n)
+        if ws_bytes == 0:
+            raise FalconError(ERR_INVALID, "batch_workspace_bytes")
+        dev = device or (self.inputs[0].device if direction == COMPRESS and n else
+                         (self.inputs[0][0].device if n else torch.device("cuda")))
+        self.workspace = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+        self.results_dev = torch.zeros(2 * max(n, 1), dtype=torch.int64, device=dev)
+        _check(L.falcon_batch_plan(direction, arr, n, self.workspace.data_ptr(), ws_bytes,
+                                   self.results_dev.data_ptr(), _stream_ptr(None)), "batch_plan")
+
+    def launch(self, stream=None) -> None:
+        _check(_load().falcon_batch_launch(self.workspace.data_ptr(), _stream_ptr(stream)), "batch_launch")
+
+    def results(self):
+        r = self.results_dev.view(-1, 2)[:len(self.inputs)].cpu().tolist()
+        return [(int(a), int(b)) for a, b in r]
+
+    def streams(self):
+        """Compressed streams (views of the output buffers) after a compress launch."""
+        return [out[:nb] for out, (nb, st) in zip(self.outputs, self.results())]
+
+    def close(self) -> None:
+        if self.workspace is not None:
+            _load().falcon_batch_forget(self.workspace.data_ptr())
+            self.workspace = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

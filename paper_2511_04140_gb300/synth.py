@@ -208,3 +208,49 @@ def adversarial_f32() -> np.ndarray:
     bits = np.array([0x7FC00001, 0xFFC00123, 0x7F800001, 0xFFA00000, 0x00000001, 0x807FFFFF],
                     dtype=np.uint32).view(np.float32)
     return np.concatenate([arr, bits])
+
+
+def series_batch_cuda(count: int = 4096, seed: int = 2, min_len: int = 1024, max_len: int = 1 << 22,
+                      p_f64: float = 0.7, max_outlier_rate: float = 0.05, device="cuda"):
+    """The independent-series workload generated on the GPU (same distributions as
+    ``series_batch``; different random stream).  Returns a list of CUDA tensors.
+
+    Each series: random walk x_{i+1} = x_i + N(0, 0.5) from 20.0, rounded to a per-series
+    number of places U{0..6} (the nearest binary value of the decimal, FP32 ties resolved
+    exactly), a per-series fraction U(0, max_outlier_rate) replaced by full-precision
+    outliers x * 10^U(3,8); FP64 with probability p_f64, else FP32."""
+    import torch
+    rng = np.random.default_rng(seed)
+    lengths = np.floor(2.0 ** rng.uniform(np.log2(min_len), np.log2(max_len), size=count)).astype(np.int64)
+    is64 = rng.random(count) < p_f64
+    places = rng.integers(0, 7, size=count)
+    rates = rng.uniform(0, max_outlier_rate, size=count)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    out = []
+    for i in range(count):
+        n = int(lengths[i])
+        steps = torch.randn(n, generator=g, device=device, dtype=torch.float64) * 0.5
+        steps[0] = 0.0
+        x = 20.0 + torch.cumsum(steps, 0)
+        p = int(places[i])
+        k = torch.round(x * (10.0 ** p))
+        d = k / (10.0 ** p)                                  # exact operands: one rounding
+        if is64[i]:
+            vals = d
+        else:
+            vals = d.to(torch.float32)
+            bits = d.view(torch.int64)
+            exp = (bits >> 52) & 0x7FF
+            tie = ((bits & ((1 << 29) - 1)) == (1 << 28)) & (exp >= 1023 - 126) & (exp <= 1023 + 127)
+            idx = torch.nonzero(tie).flatten()
+            if idx.numel():
+                fixed = decimal_to_f32(k[idx].to(torch.int64).cpu().numpy(), p)
+                vals[idx] = torch.from_numpy(fixed).to(device)
+        mask = torch.rand(n, generator=g, device=device) < float(rates[i])
+        if bool(mask.any()):
+            u = torch.rand(n, generator=g, device=device, dtype=torch.float64) * 5 + 3
+            big = (x * torch.pow(10.0, u)).to(vals.dtype)
+            vals = torch.where(mask, big, vals)
+        out.append(vals.contiguous())
+    return out
