@@ -43,6 +43,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-pipeline", action="store_true")
+    ap.add_argument("--pipeline-values", type=int, default=1 << 31, help=argparse.SUPPRESS)
     ap.add_argument("--batch-series", type=int, default=4096, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -307,6 +309,9 @@ def main():
         del bufs, host
         torch.cuda.empty_cache()
         line["batched"] = bench_batched(falcon, synth, torch, dev, args.batch_series)
+    if rank == 0 and not args.no_pipeline:
+        torch.cuda.empty_cache()
+        line["pipeline"] = bench_pipeline(falcon, synth, torch, dev, args.pipeline_values)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     if rank == 0:
@@ -395,45 +400,87 @@ def bench_batched(falcon, synth, torch, dev, count):
     return out
 
 
+def host_link(torch, dev, nbytes=1 << 30):
+    """Pinned-memory copy bandwidth in each direction (GB/s), for the end-to-end fractions."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, fn in (("h2d", lambda: d.copy_(h, non_blocking=True)), ("d2h", lambda: h.copy_(d, non_blocking=True))):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize(dev)
+        out[name] = 3 * nbytes / (time.perf_counter() - t0) / 1e9
+    return out
+
+
 def e2e(falcon, torch, bufs, host, dev, args):
-    """Same metric through the public API with host buffers: pinned H2D of the values,
-    compress, D2H of the stream, H2D of the stream, decompress, D2H of the values."""
-    pinned = {}
-    for dt, arr in host.items():
-        b = bufs[dt]
-        pinned[dt] = dict(x=torch.from_numpy(arr).pin_memory(),
-                          s=torch.empty(b["out"].numel(), dtype=torch.uint8).pin_memory(),
-                          y=torch.empty(len(arr), dtype=b["x"].dtype).pin_memory())
-    stream = torch.cuda.current_stream(dev)
+    """Same metric through the public host-memory API: the streaming pipeline (H2D ->
+    compress -> D2H, then H2D -> decompress -> D2H, 64 MiB frames, 16 streams) on pinned
+    buffers; host-to-host time."""
+    frame_bytes = 64 << 20
+    pinned = {dt: torch.from_numpy(arr).pin_memory() for dt, arr in host.items()}
+    outs = {}
 
     def one():
         h2d = d2h = 0
-        for dt, p in pinned.items():
-            b = bufs[dt]
-            b["x"].copy_(p["x"], non_blocking=True)
-            h2d += p["x"].numel() * p["x"].element_size()
-            s = falcon.compress(b["x"], BLOCK, out=b["out"])
-            nb = s.numel()
-            p["s"][:nb].copy_(s, non_blocking=True)
-            d2h += nb
-            b["out"][:nb].copy_(p["s"][:nb], non_blocking=True)
-            h2d += nb
-            y = falcon.decompress(b["out"][:nb], out=b["y"])
-            p["y"].copy_(y, non_blocking=True)
-            d2h += p["y"].numel() * p["y"].element_size()
+        for dt, x in pinned.items():
+            fv = frame_bytes // x.element_size()
+            s, fb = falcon.pipeline_compress(x, block=BLOCK, frame_values=fv, nstreams=16, out=outs.get(dt))
+            outs.setdefault(dt, s._base if s._base is not None else s)
+            y = falcon.pipeline_decompress(s, fb, nstreams=16)
+            h2d += x.numel() * x.element_size() + s.numel()
+            d2h += s.numel() + y.numel() * y.element_size()
         return h2d, d2h
 
     one()
-    torch.cuda.synchronize(dev)
     reps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(reps):
         h2d, d2h = one()
-    torch.cuda.synchronize(dev)
     dt = (time.perf_counter() - t0) / reps
     orig = sum(a.nbytes for a in host.values())
     return {"value": 2 * orig / dt / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "mode": "sequential H2D -> compress -> D2H -> H2D -> decompress -> D2H, pinned host buffers"}
+            "mode": "falcon_pipeline_compress + falcon_pipeline_decompress, host to host, pinned buffers, "
+                    "64 MiB frames, 16 streams", "host_link": host_link(torch, dev)}
+
+
+def bench_pipeline(falcon, synth, torch, dev, n):
+    """2^31 FP64 values (16 GiB) in pinned host memory - random walk with 3 decimal places and
+    0.5% full-precision outliers - streamed through the GPU in 64 MiB frames and back."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(4)
+    x = 20.0 + torch.cumsum(torch.randn(n, generator=g, device=dev, dtype=torch.float64) * 0.5, 0)
+    vals = torch.round(x * 1000.0) / 1000.0
+    mask = torch.rand(n, generator=g, device=dev) < 0.005
+    vals = torch.where(mask, x * torch.pow(10.0, torch.rand(n, generator=g, device=dev, dtype=torch.float64) * 5 + 3), vals)
+    del x, mask
+    t0 = time.perf_counter()
+    h = torch.empty(n, dtype=torch.float64).pin_memory()
+    h.copy_(vals)
+    del vals
+    torch.cuda.empty_cache()
+    out = torch.empty(((n + (1 << 23) - 1) >> 23) * falcon.bound(1 << 23, falcon.F64, BLOCK), dtype=torch.uint8).pin_memory()
+    back = torch.empty(n, dtype=torch.float64).pin_memory()
+    setup_s = time.perf_counter() - t0
+    falcon.pipeline_compress(h[:1 << 24], block=BLOCK, frame_values=1 << 23, nstreams=16, out=out)   # warm-up
+    t0 = time.perf_counter()
+    s, fb = falcon.pipeline_compress(h, block=BLOCK, frame_values=1 << 23, nstreams=16, out=out)
+    tc = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    y = falcon.pipeline_decompress(s, fb, nstreams=16, out=back)
+    td = time.perf_counter() - t0
+    ok = bool(torch.equal(y.view(torch.int64), h.view(torch.int64)))
+    link = host_link(torch, dev)
+    nbytes = n * 8
+    return {"workload": f"{n} FP64 values ({nbytes / 2**30:.1f} GiB) in pinned host memory, random walk, "
+                        "3 places, 0.5% outliers; 64 MiB frames, 16 streams",
+            "compress_gbs": nbytes / tc / 1e9, "decompress_gbs": nbytes / td / 1e9, "ratio": s.numel() / nbytes,
+            "frames": len(fb), "bit_exact": ok, "host_link_gbs": link,
+            "compress_frac_of_h2d": nbytes / tc / 1e9 / link["h2d"],
+            "decompress_frac_of_d2h": nbytes / td / 1e9 / link["d2h"], "setup_s": setup_s}
 
 
 if __name__ == "__main__":

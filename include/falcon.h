@@ -159,6 +159,31 @@ int falcon_batch_launch(void *d_workspace, void *stream);
 /* Drops the host-side record of the plan held by d_workspace. */
 int falcon_batch_forget(void *d_workspace);
 
+/* ---------------------------------------------------------------------------------------
+ * Host <-> device streaming (Sec. 3.1, Alg. 1).  Values in HOST memory are cut into frames of
+ * frame_values values; each frame goes H2D -> compress -> D2H on one of nstreams CUDA
+ * streams.  As in the paper's event-driven scheduler, a frame's place in the output is
+ * fixed in launch order as soon as its compressed size has come back (the "M-D2H"), so the
+ * payload copy ("P-D2H") of frame f overlaps the upload and compression of later frames and
+ * the output needs no merging pass.  Every frame is a complete stream; the frames are
+ * concatenated in h_out.  Host buffers should be page-locked (cudaHostAlloc) for the copies
+ * to overlap; pageable memory works but serialises them.  The device buffers are allocated
+ * per call (nstreams x (frame input + frame bound + workspace)) and freed before returning.
+ * ------------------------------------------------------------------------------------- */
+
+/* Compresses n values at h_in.  h_frame_bytes (host, ceil(n / frame_values) entries)
+ * receives each frame's stream length; *out_bytes the total.  FALCON_ERR_CAPACITY if the
+ * frames do not fit in out_capacity bytes. */
+int falcon_pipeline_compress(const void *h_in, uint64_t n, int dtype, uint32_t block_size,
+                             uint64_t frame_values, int nstreams, void *h_out, size_t out_capacity,
+                             uint64_t *h_frame_bytes, size_t *out_bytes);
+
+/* Decompresses nframes concatenated streams (lengths in h_frame_bytes) from h_in into h_out.
+ * Output positions follow from the frame headers, so frames are processed fully in
+ * parallel (the pre-allocation scheduler of Sec. 4).  *n_out receives the value count. */
+int falcon_pipeline_decompress(const void *h_in, const uint64_t *h_frame_bytes, uint64_t nframes,
+                               int nstreams, void *h_out, size_t out_capacity_bytes, uint64_t *n_out);
+
 /* Persistent-grid size: at most ctas_per_sm resident CTAs per SM for each direction
  * (0 = as many as fit).  Does not change any output byte; used by the autotuner. */
 int falcon_set_launch_config(int compress_ctas_per_sm, int decompress_ctas_per_sm);

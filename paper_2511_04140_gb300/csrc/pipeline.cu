@@ -1,0 +1,214 @@
+// Host <-> device streaming pipeline (Sec. 3.1, Alg. 1 of the paper): host code only.
+//
+// Compression follows the event-driven scheduler: every CUDA stream slot cycles through
+//   Idle   -> H2D(frame) ; compress (async) ; D2H(16-byte result) ; event      -> MPend
+//   MPend  -> (when this frame is the next one to be placed and its event fired)
+//             offset fixed ; D2H(payload -> h_out + offset) ; event            -> PPend
+//   PPend  -> (event fired)                                                    -> Idle
+// Frames are launched round-robin on the slots, so launch order = frame order and the
+// slot holding the next frame to be placed is simply frame % nstreams.
+// Decompression knows every frame's output position from its header (pre-allocation), so
+// each slot runs H2D -> decompress -> D2H without ordering between slots.
+#include <cstring>
+#include <vector>
+
+#include "falcon.h"
+#include "falcon_internal.h"
+
+namespace {
+
+enum SlotState { kIdle, kMPend, kPPend };
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    uint8_t *d_in = nullptr;
+    uint8_t *d_out = nullptr;
+    uint8_t *d_ws = nullptr;
+    uint64_t *d_res = nullptr;
+    uint64_t *h_res = nullptr;        // pinned
+    cudaEvent_t ev = nullptr;
+    SlotState state = kIdle;
+    uint64_t frame = 0;
+};
+
+struct SlotSet {
+    std::vector<Slot> slots;
+    ~SlotSet() {
+        for (Slot &s : slots) {
+            if (s.stream) cudaStreamSynchronize(s.stream);
+            if (s.ev) cudaEventDestroy(s.ev);
+            if (s.stream) cudaStreamDestroy(s.stream);
+            cudaFree(s.d_in);
+            cudaFree(s.d_out);
+            cudaFree(s.d_ws);
+            cudaFree(s.d_res);
+            if (s.h_res) cudaFreeHost(s.h_res);
+        }
+    }
+    int init(int n, size_t in_bytes, size_t out_bytes, size_t ws_bytes) {
+        slots.resize((size_t)n);
+        for (Slot &s : slots) {
+            if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) return FALCON_ERR_CUDA;
+            if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) return FALCON_ERR_CUDA;
+            if (cudaMalloc(&s.d_in, in_bytes ? in_bytes : 16) != cudaSuccess) return FALCON_ERR_CUDA;
+            if (cudaMalloc(&s.d_out, out_bytes ? out_bytes : 16) != cudaSuccess) return FALCON_ERR_CUDA;
+            if (cudaMalloc(&s.d_ws, ws_bytes) != cudaSuccess) return FALCON_ERR_CUDA;
+            if (cudaMalloc(&s.d_res, 16) != cudaSuccess) return FALCON_ERR_CUDA;
+            if (cudaHostAlloc(&s.h_res, 16, cudaHostAllocDefault) != cudaSuccess) return FALCON_ERR_CUDA;
+        }
+        return FALCON_OK;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+int falcon_pipeline_compress(const void *h_in, uint64_t n, int dtype, uint32_t block_size, uint64_t frame_values,
+                             int nstreams, void *h_out, size_t out_capacity, uint64_t *h_frame_bytes,
+                             size_t *out_bytes) {
+    if ((dtype != FALCON_F64 && dtype != FALCON_F32) || !h_out || !out_bytes || !h_frame_bytes) return FALCON_ERR_INVALID;
+    if (n > 0 && !h_in) return FALCON_ERR_INVALID;
+    if (frame_values == 0 || nstreams < 1 || nstreams > 256) return FALCON_ERR_INVALID;
+    if (falcon_bound(frame_values, dtype, block_size) == 0) return FALCON_ERR_INVALID;
+    if (block_size > falcon::kMaxBlock) return FALCON_ERR_UNSUPPORTED;
+    const size_t s = dtype == FALCON_F64 ? 8 : 4;
+    const uint64_t nframes = (n + frame_values - 1) / frame_values;
+    const uint64_t fchunks = (frame_values + block_size - 1) / block_size;
+    const size_t fbound = falcon_bound(frame_values, dtype, block_size);
+    SlotSet set;
+    int st = set.init((int)(nframes < (uint64_t)nstreams ? (nframes ? nframes : 1) : (uint64_t)nstreams),
+                      frame_values * s, fbound, falcon_workspace_bytes(fchunks));
+    if (st) return st;
+    const uint64_t ns = set.slots.size();
+    const uint8_t *in8 = static_cast<const uint8_t *>(h_in);
+    uint8_t *out8 = static_cast<uint8_t *>(h_out);
+    uint64_t next = 0, placed = 0, done = 0;
+    size_t offset = 0;
+    int status = FALCON_OK;
+    while (done < nframes) {
+        for (uint64_t i = 0; i < ns; ++i) {
+            Slot &sl = set.slots[i];
+            if (sl.state == kIdle) {
+                if (next < nframes && next % ns == i && status == FALCON_OK) {
+                    const uint64_t first = next * frame_values;
+                    const uint64_t m = (n - first) < frame_values ? (n - first) : frame_values;
+                    if (cudaMemcpyAsync(sl.d_in, in8 + first * s, m * s, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+                        return FALCON_ERR_CUDA;
+                    st = falcon_compress_async(sl.d_in, m, dtype, block_size, sl.d_out, fbound, sl.d_ws,
+                                               falcon_workspace_bytes(fchunks), sl.d_res, sl.stream);
+                    if (st) return st;
+                    if (cudaMemcpyAsync(sl.h_res, sl.d_res, 16, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+                        return FALCON_ERR_CUDA;
+                    if (cudaEventRecord(sl.ev, sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+                    sl.frame = next++;
+                    sl.state = kMPend;
+                }
+            } else if (sl.state == kMPend) {
+                if (sl.frame != placed) continue;                 // offsets are fixed in launch order
+                const cudaError_t q = cudaEventQuery(sl.ev);
+                if (q == cudaErrorNotReady) continue;
+                if (q != cudaSuccess) return FALCON_ERR_CUDA;
+                const uint64_t cs = sl.h_res[0];
+                if (sl.h_res[1] != 0 && status == FALCON_OK) status = (int)sl.h_res[1];
+                if (status == FALCON_OK && offset + cs > out_capacity) status = FALCON_ERR_CAPACITY;
+                h_frame_bytes[sl.frame] = cs;
+                if (status == FALCON_OK &&
+                    cudaMemcpyAsync(out8 + offset, sl.d_out, cs, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+                    return FALCON_ERR_CUDA;
+                if (cudaEventRecord(sl.ev, sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+                offset += cs;
+                ++placed;
+                sl.state = kPPend;
+            } else {
+                const cudaError_t q = cudaEventQuery(sl.ev);
+                if (q == cudaErrorNotReady) continue;
+                if (q != cudaSuccess) return FALCON_ERR_CUDA;
+                sl.state = kIdle;
+                ++done;
+            }
+        }
+        if (status != FALCON_OK && placed == next) break;       // nothing left in flight to place
+    }
+    for (Slot &sl : set.slots)
+        if (cudaStreamSynchronize(sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+    if (status != FALCON_OK) return status;
+    *out_bytes = offset;
+    return FALCON_OK;
+}
+
+int falcon_pipeline_decompress(const void *h_in, const uint64_t *h_frame_bytes, uint64_t nframes, int nstreams,
+                               void *h_out, size_t out_capacity_bytes, uint64_t *n_out) {
+    if (!h_frame_bytes || !n_out || (nframes > 0 && (!h_in || !h_out))) return FALCON_ERR_INVALID;
+    if (nstreams < 1 || nstreams > 256) return FALCON_ERR_INVALID;
+    const uint8_t *in8 = static_cast<const uint8_t *>(h_in);
+    uint8_t *out8 = static_cast<uint8_t *>(h_out);
+    // frame positions from the headers (host memory)
+    std::vector<uint64_t> in_off(nframes), out_off(nframes), nvals(nframes);
+    uint64_t ioff = 0, ooff = 0, total = 0;
+    size_t max_in = 16, max_vals = 1, max_chunks = 0;
+    for (uint64_t f = 0; f < nframes; ++f) {
+        if (h_frame_bytes[f] < FALCON_HEADER_BYTES) return FALCON_ERR_CORRUPT;
+        uint64_t nv = 0, nc = 0;
+        int dt = 0;
+        uint32_t blk = 0;
+        const int st = falcon_stream_info(in8 + ioff, h_frame_bytes[f], &nv, &dt, &blk, &nc);
+        if (st) return st;
+        const size_t s = dt == FALCON_F64 ? 8 : 4;
+        in_off[f] = ioff;
+        out_off[f] = ooff;
+        nvals[f] = nv;
+        ioff += h_frame_bytes[f];
+        ooff += nv * s;
+        total += nv;
+        if (h_frame_bytes[f] > max_in) max_in = h_frame_bytes[f];
+        if (nv * s > max_vals) max_vals = nv * s;
+        if (nc > max_chunks) max_chunks = nc;
+    }
+    if (ooff > out_capacity_bytes) return FALCON_ERR_CAPACITY;
+    SlotSet set;
+    int st = set.init((int)(nframes < (uint64_t)nstreams ? (nframes ? nframes : 1) : (uint64_t)nstreams),
+                      (max_in + 15) / 16 * 16, max_vals, falcon_workspace_bytes(max_chunks));
+    if (st) return st;
+    const uint64_t ns = set.slots.size();
+    uint64_t next = 0, done = 0;
+    int status = FALCON_OK;
+    while (done < nframes) {
+        for (uint64_t i = 0; i < ns; ++i) {
+            Slot &sl = set.slots[i];
+            if (sl.state == kIdle) {
+                if (next < nframes && status == FALCON_OK) {
+                    const uint64_t f = next++;
+                    if (cudaMemcpyAsync(sl.d_in, in8 + in_off[f], h_frame_bytes[f], cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+                        return FALCON_ERR_CUDA;
+                    st = falcon_decompress_async(sl.d_in, h_frame_bytes[f], in8 + in_off[f], sl.d_out, max_vals, sl.d_ws,
+                                                 falcon_workspace_bytes(max_chunks), sl.d_res, sl.stream);
+                    if (st) return st;
+                    const size_t s = (in8[in_off[f] + 5] == FALCON_F64) ? 8 : 4;
+                    if (cudaMemcpyAsync(out8 + out_off[f], sl.d_out, nvals[f] * s, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+                        return FALCON_ERR_CUDA;
+                    if (cudaMemcpyAsync(sl.h_res, sl.d_res, 16, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+                        return FALCON_ERR_CUDA;
+                    if (cudaEventRecord(sl.ev, sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+                    sl.frame = f;
+                    sl.state = kPPend;
+                }
+            } else {
+                const cudaError_t q = cudaEventQuery(sl.ev);
+                if (q == cudaErrorNotReady) continue;
+                if (q != cudaSuccess) return FALCON_ERR_CUDA;
+                if (sl.h_res[1] != 0 && status == FALCON_OK) status = (int)sl.h_res[1];
+                sl.state = kIdle;
+                ++done;
+            }
+        }
+        if (status != FALCON_OK && done == next) break;
+    }
+    for (Slot &sl : set.slots)
+        if (cudaStreamSynchronize(sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+    if (status != FALCON_OK) return status;
+    *n_out = total;
+    return FALCON_OK;
+}
+
+}  // extern "C"

@@ -77,6 +77,10 @@ def _load():
             L.falcon_batch_forget.argtypes = [vp]
             L.falcon_set_launch_config.restype = ci
             L.falcon_set_launch_config.argtypes = [ci, ci]
+            L.falcon_pipeline_compress.restype = ci
+            L.falcon_pipeline_compress.argtypes = [vp, u64, ci, u32, u64, ci, vp, sz, vp, c.POINTER(sz)]
+            L.falcon_pipeline_decompress.restype = ci
+            L.falcon_pipeline_decompress.argtypes = [vp, vp, u64, ci, vp, sz, c.POINTER(u64)]
             _lib = L
     return _lib
 
@@ -253,3 +257,44 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def pipeline_compress(x: torch.Tensor, block: int = 1024, frame_values: int = 1 << 23, nstreams: int = 16,
+                      out: torch.Tensor | None = None):
+    """Streams a HOST tensor (pin it for overlap) through the GPU in frames; returns
+    (uint8 host tensor of the concatenated frame streams, list of frame lengths)."""
+    if x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous host tensor")
+    code = _dtype_code(x)
+    n = x.numel()
+    nframes = (n + frame_values - 1) // frame_values
+    if out is None:
+        cap = nframes * bound(frame_values, code, block) if nframes else 32
+        out = torch.empty(cap, dtype=torch.uint8, pin_memory=torch.cuda.is_available())
+    fb = (ctypes.c_uint64 * max(nframes, 1))()
+    total = ctypes.c_size_t()
+    _check(_load().falcon_pipeline_compress(x.data_ptr(), n, code, block, frame_values, nstreams, out.data_ptr(),
+                                            out.numel(), fb, ctypes.byref(total)), "pipeline_compress")
+    return out[:total.value], [int(fb[i]) for i in range(nframes)]
+
+
+def pipeline_decompress(s: torch.Tensor, frame_bytes, nstreams: int = 16, out: torch.Tensor | None = None,
+                        dtype=None, n: int | None = None) -> torch.Tensor:
+    """Inverse of pipeline_compress: host frames -> host values."""
+    nframes = len(frame_bytes)
+    fb = (ctypes.c_uint64 * max(nframes, 1))(*frame_bytes)
+    if out is None:
+        if n is None or dtype is None:
+            tot, code = 0, F64
+            off = 0
+            for b in frame_bytes:
+                nv, code, _, _ = stream_info(s[off:off + HEADER_BYTES].numpy().tobytes())
+                tot += nv
+                off += b
+            n, dtype = tot, (torch.float64 if code == F64 else torch.float32)
+        out = torch.empty(max(n, 1), dtype=dtype, pin_memory=torch.cuda.is_available())
+    n_out = ctypes.c_uint64()
+    _check(_load().falcon_pipeline_decompress(s.data_ptr(), fb, nframes, nstreams, out.data_ptr(),
+                                              out.numel() * out.element_size(), ctypes.byref(n_out)),
+           "pipeline_decompress")
+    return out[:n_out.value]

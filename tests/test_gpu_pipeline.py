@@ -1,0 +1,64 @@
+"""Host <-> device streaming pipeline (Sec. 3.1, Alg. 1): every frame of the output is the
+oracle's stream for that frame's values, frames are placed in launch order, and the
+inverse pipeline restores every bit."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2511_04140_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2511_04140_gb300 import build
+    build.build()
+    from paper_2511_04140_gb300 import falcon
+    return falcon
+
+
+def _u(a):
+    return a.view(np.uint64 if a.dtype == np.float64 else np.uint32)
+
+
+@pytest.mark.parametrize("nstreams", [1, 3, 16])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_pipeline_frames_match_oracle(F, oracle, nstreams, dtype):
+    vals = synth.segments(700_001, seed=12, dtype=dtype)
+    frame = 65_536
+    x = torch.from_numpy(vals).pin_memory()
+    s, fb = F.pipeline_compress(x, block=1024, frame_values=frame, nstreams=nstreams)
+    assert len(fb) == (len(vals) + frame - 1) // frame
+    blob = s.numpy().tobytes()
+    off = 0
+    for i, nb in enumerate(fb):
+        part = vals[i * frame:(i + 1) * frame]
+        assert blob[off:off + nb] == oracle.compress(part, 1024), i
+        off += nb
+    assert off == len(blob)
+    y = F.pipeline_decompress(s, fb, nstreams=nstreams)
+    assert np.array_equal(_u(y.numpy()), _u(vals))
+
+
+def test_pipeline_pageable_and_tail(F, oracle):
+    vals = synth.random_walk(100_003, seed=7, places=3, outlier_rate=0.005)
+    x = torch.from_numpy(vals)                     # pageable: copies serialise, bytes identical
+    s, fb = F.pipeline_compress(x, block=1025, frame_values=30_000, nstreams=2)
+    blob = s.numpy().tobytes()
+    off = 0
+    for i, nb in enumerate(fb):
+        assert blob[off:off + nb] == oracle.compress(vals[i * 30_000:(i + 1) * 30_000], 1025)
+        off += nb
+    y = F.pipeline_decompress(s, fb, nstreams=2)
+    assert np.array_equal(_u(y.numpy()), _u(vals))
+
+
+def test_pipeline_capacity(F):
+    vals = synth.segments(200_000, seed=3)
+    x = torch.from_numpy(vals).pin_memory()
+    out = torch.empty(100_000, dtype=torch.uint8).pin_memory()
+    with pytest.raises(F.FalconError) as e:
+        F.pipeline_compress(x, block=1024, frame_values=50_000, nstreams=4, out=out)
+    assert e.value.status == F.ERR_CAPACITY
