@@ -44,6 +44,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help=argparse.SUPPRESS)
+    ap.add_argument("--serve-rates", default="1000,5000", help=argparse.SUPPRESS)
     ap.add_argument("--pipeline-values", type=int, default=1 << 31, help=argparse.SUPPRESS)
     ap.add_argument("--batch-series", type=int, default=4096, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -312,6 +315,9 @@ def main():
     if rank == 0 and not args.no_pipeline:
         torch.cuda.empty_cache()
         line["pipeline"] = bench_pipeline(falcon, synth, torch, dev, args.pipeline_values)
+    if rank == 0 and not args.no_serve:
+        torch.cuda.empty_cache()
+        line["serve"] = bench_serve(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(n)
     if rank == 0:
@@ -397,6 +403,23 @@ def bench_batched(falcon, synth, torch, dev, count):
     comp.close()
     dec.close()
     falcon.set_launch_config(0, 0)
+    return out
+
+
+def bench_serve(args, dev):
+    """Poisson arrivals, 50/50 compress/decompress, request sizes log-uniform 4 KB..256 MB,
+    FP64/FP32 50/50, random-walk data; 64 GB device-memory admission budget.  Each offered
+    load is served by the continuous-batching server and, as the baseline, one request at a
+    time.  The run length per load is shortened from 60 s to keep the bench within minutes."""
+    from paper_2511_04140_gb300 import serve
+    pool = serve.make_pool(count=32, device=dev)
+    out = {"workload": f"{len(pool)}-request pool, sizes log-uniform 4 KB..256 MB, {args.serve_seconds:g} s per load",
+           "loads": []}
+    for rate in [float(r) for r in args.serve_rates.split(",")]:
+        with serve.Server(budget_bytes=64 << 30, device=dev) as srv:
+            r = serve.run_load(srv, pool, rate=rate, duration=args.serve_seconds, seed=int(rate))
+        b = serve.run_one_at_a_time(pool, rate=rate, duration=args.serve_seconds, seed=int(rate), device=dev)
+        out["loads"].append({"offered_req_s": rate, "server": r, "one_at_a_time": b})
     return out
 
 

@@ -10,6 +10,8 @@
 
 using namespace falcon;
 
+void falcon_pipeline_release();
+
 namespace falcon {
 int g_ctas_per_sm[2] = {0, 0};
 }
@@ -301,6 +303,7 @@ int falcon_release(void) {
     }
     g_ws.clear();
     cudaSetDevice(cur);
+    falcon_pipeline_release();
     return FALCON_OK;
 }
 

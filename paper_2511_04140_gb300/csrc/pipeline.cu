@@ -10,6 +10,8 @@
 // Decompression knows every frame's output position from its header (pre-allocation), so
 // each slot runs H2D -> decompress -> D2H without ordering between slots.
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include <vector>
 
 #include "falcon.h"
@@ -60,7 +62,60 @@ struct SlotSet {
     }
 };
 
+// Slot sets are kept between calls (per device): allocating a frame's buffers on every
+// call would cost more than streaming a few frames.  One call uses a set at a time.
+struct CachedSet {
+    std::mutex mu;
+    std::unique_ptr<SlotSet> set;
+    int n = 0;
+    size_t in_bytes = 0, out_bytes = 0, ws_bytes = 0;
+};
+std::mutex g_cache_mu;
+CachedSet g_cache[64];
+
+int acquire_slots(int n, size_t in_bytes, size_t out_bytes, size_t ws_bytes, std::unique_lock<std::mutex> &hold,
+                  SlotSet *&out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FALCON_ERR_CUDA;
+    CachedSet &c = g_cache[dev & 63];
+    hold = std::unique_lock<std::mutex>(c.mu);
+    if (!c.set || c.n < n || c.in_bytes < in_bytes || c.out_bytes < out_bytes || c.ws_bytes < ws_bytes) {
+        c.set.reset();
+        c.set.reset(new SlotSet());
+        c.n = n > c.n ? n : c.n;
+        c.in_bytes = in_bytes > c.in_bytes ? in_bytes : c.in_bytes;
+        c.out_bytes = out_bytes > c.out_bytes ? out_bytes : c.out_bytes;
+        c.ws_bytes = ws_bytes > c.ws_bytes ? ws_bytes : c.ws_bytes;
+        const int st = c.set->init(c.n, c.in_bytes, c.out_bytes, c.ws_bytes);
+        if (st) {
+            c.set.reset();
+            c.n = 0;
+            c.in_bytes = c.out_bytes = c.ws_bytes = 0;
+            return st;
+        }
+    }
+    for (Slot &sl : c.set->slots) sl.state = kIdle;
+    out = c.set.get();
+    return FALCON_OK;
+}
+
 }  // namespace
+
+// Frees the cached pipeline buffers of every device (called by falcon_release).
+void falcon_pipeline_release() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (int d = 0; d < 64; ++d) {
+        std::lock_guard<std::mutex> lk(g_cache[d].mu);
+        if (g_cache[d].set) {
+            cudaSetDevice(d);
+            g_cache[d].set.reset();
+            g_cache[d].n = 0;
+            g_cache[d].in_bytes = g_cache[d].out_bytes = g_cache[d].ws_bytes = 0;
+        }
+    }
+    cudaSetDevice(cur);
+}
 
 extern "C" {
 
@@ -76,11 +131,13 @@ int falcon_pipeline_compress(const void *h_in, uint64_t n, int dtype, uint32_t b
     const uint64_t nframes = (n + frame_values - 1) / frame_values;
     const uint64_t fchunks = (frame_values + block_size - 1) / block_size;
     const size_t fbound = falcon_bound(frame_values, dtype, block_size);
-    SlotSet set;
-    int st = set.init((int)(nframes < (uint64_t)nstreams ? (nframes ? nframes : 1) : (uint64_t)nstreams),
-                      frame_values * s, fbound, falcon_workspace_bytes(fchunks));
+    std::unique_lock<std::mutex> hold;
+    SlotSet *setp = nullptr;
+    const int want = (int)(nframes < (uint64_t)nstreams ? (nframes ? nframes : 1) : (uint64_t)nstreams);
+    int st = acquire_slots(want, frame_values * s, fbound, falcon_workspace_bytes(fchunks), hold, setp);
     if (st) return st;
-    const uint64_t ns = set.slots.size();
+    SlotSet &set = *setp;
+    const uint64_t ns = (uint64_t)want;
     const uint8_t *in8 = static_cast<const uint8_t *>(h_in);
     uint8_t *out8 = static_cast<uint8_t *>(h_out);
     uint64_t next = 0, placed = 0, done = 0;
@@ -130,8 +187,8 @@ int falcon_pipeline_compress(const void *h_in, uint64_t n, int dtype, uint32_t b
         }
         if (status != FALCON_OK && placed == next) break;       // nothing left in flight to place
     }
-    for (Slot &sl : set.slots)
-        if (cudaStreamSynchronize(sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+    for (uint64_t i = 0; i < ns; ++i)
+        if (cudaStreamSynchronize(set.slots[i].stream) != cudaSuccess) return FALCON_ERR_CUDA;
     if (status != FALCON_OK) return status;
     *out_bytes = offset;
     return FALCON_OK;
@@ -166,11 +223,13 @@ int falcon_pipeline_decompress(const void *h_in, const uint64_t *h_frame_bytes, 
         if (nc > max_chunks) max_chunks = nc;
     }
     if (ooff > out_capacity_bytes) return FALCON_ERR_CAPACITY;
-    SlotSet set;
-    int st = set.init((int)(nframes < (uint64_t)nstreams ? (nframes ? nframes : 1) : (uint64_t)nstreams),
-                      (max_in + 15) / 16 * 16, max_vals, falcon_workspace_bytes(max_chunks));
+    std::unique_lock<std::mutex> hold;
+    SlotSet *setp = nullptr;
+    const int want = (int)(nframes < (uint64_t)nstreams ? (nframes ? nframes : 1) : (uint64_t)nstreams);
+    int st = acquire_slots(want, (max_in + 15) / 16 * 16, max_vals, falcon_workspace_bytes(max_chunks), hold, setp);
     if (st) return st;
-    const uint64_t ns = set.slots.size();
+    SlotSet &set = *setp;
+    const uint64_t ns = (uint64_t)want;
     uint64_t next = 0, done = 0;
     int status = FALCON_OK;
     while (done < nframes) {
@@ -204,8 +263,8 @@ int falcon_pipeline_decompress(const void *h_in, const uint64_t *h_frame_bytes, 
         }
         if (status != FALCON_OK && done == next) break;
     }
-    for (Slot &sl : set.slots)
-        if (cudaStreamSynchronize(sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+    for (uint64_t i = 0; i < ns; ++i)
+        if (cudaStreamSynchronize(set.slots[i].stream) != cudaSuccess) return FALCON_ERR_CUDA;
     if (status != FALCON_OK) return status;
     *n_out = total;
     return FALCON_OK;
