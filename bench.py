@@ -45,8 +45,8 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help=argparse.SUPPRESS)
-    ap.add_argument("--serve-rates", default="1000,5000", help=argparse.SUPPRESS)
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help=argparse.SUPPRESS)
+    ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000", help=argparse.SUPPRESS)
     ap.add_argument("--pipeline-values", type=int, default=1 << 31, help=argparse.SUPPRESS)
     ap.add_argument("--batch-series", type=int, default=4096, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -180,6 +180,26 @@ def cpu_baseline(n):
                       f"compress + decompress, single thread, {dt:.1f} s"}
 
 
+def release_caches(torch):
+    """Return cached device and pinned host blocks between bench sections (torch's pinned-host
+    cache rounds blocks up to powers of two and otherwise keeps them for the process)."""
+    import gc
+    gc.collect()
+    torch.cuda.empty_cache()
+    getattr(torch._C, "_host_emptyCache", lambda: None)()
+
+
+def progress(stage):
+    """One line per bench stage on stderr (elapsed seconds, peak host RSS)."""
+    import resource
+    rss = resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 2**20
+    sys.stderr.write(f"[bench {time.perf_counter() - _T0:7.1f} s, peak rss {rss:5.1f} GiB] {stage}\n")
+    sys.stderr.flush()
+
+
+_T0 = time.perf_counter()
+
+
 # ------------------------------------------------------------------------------ falcon arm
 def main():
     args = parse_args()
@@ -203,6 +223,7 @@ def main():
     from paper_2511_04140_gb300 import falcon, synth
 
     n = args.n
+    progress("generating inputs")
     host = {np.float64: synth.segments(n, seed=1), np.float32: synth.segments(n, seed=1, dtype=np.float32)}
     stream = torch.cuda.Stream(device=dev)
     st_ptr = stream
@@ -240,6 +261,7 @@ def main():
             if events is not None:
                 events[i][1].record(stream)
 
+    progress("inputs resident; kernel steps")
     clocks = ClockSampler(local)
     clocks.start()
     with torch.cuda.stream(stream):
@@ -307,18 +329,25 @@ def main():
         "clocks": clocks.summary(),
     }
     if rank == 0 and not args.no_e2e:
+        progress("end-to-end pipeline")
         line["e2e"] = e2e(falcon, torch, bufs, host, dev, args)
     if rank == 0 and not args.no_batched:
         del bufs, host
         torch.cuda.empty_cache()
+        progress("batched launch")
         line["batched"] = bench_batched(falcon, synth, torch, dev, args.batch_series)
-    if rank == 0 and not args.no_pipeline:
-        torch.cuda.empty_cache()
-        line["pipeline"] = bench_pipeline(falcon, synth, torch, dev, args.pipeline_values)
     if rank == 0 and not args.no_serve:
-        torch.cuda.empty_cache()
+        release_caches(torch)
+        progress("server")
         line["serve"] = bench_serve(args, dev)
+        release_caches(torch)
+    if rank == 0 and not args.no_pipeline:
+        release_caches(torch)
+        progress("host pipeline")
+        line["pipeline"] = bench_pipeline(falcon, synth, torch, dev, args.pipeline_values)
+        release_caches(torch)
     if rank == 0 and not args.no_cpu_baseline:
+        progress("cpu baseline")
         line["cpu_baseline"] = cpu_baseline(n)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -408,18 +437,31 @@ def bench_batched(falcon, synth, torch, dev, count):
 
 def bench_serve(args, dev):
     """Poisson arrivals, 50/50 compress/decompress, request sizes log-uniform 4 KB..256 MB,
-    FP64/FP32 50/50, random-walk data; 64 GB device-memory admission budget.  Each offered
-    load is served by the continuous-batching server and, as the baseline, one request at a
-    time.  The run length per load is shortened from 60 s to keep the bench within minutes."""
+    FP64/FP32 50/50, random-walk data (2 places); 64 GB device-memory admission budget.  Each
+    offered load is served by the continuous-batching server and, as the baseline, one request
+    at a time.  Each load runs for --serve-seconds (shortened from 60 s to keep the bench
+    within minutes).  Latency: scheduled arrival -> result seen by the client."""
     from paper_2511_04140_gb300 import serve
     pool = serve.make_pool(count=32, device=dev)
-    out = {"workload": f"{len(pool)}-request pool, sizes log-uniform 4 KB..256 MB, {args.serve_seconds:g} s per load",
-           "loads": []}
-    for rate in [float(r) for r in args.serve_rates.split(",")]:
-        with serve.Server(budget_bytes=64 << 30, device=dev) as srv:
-            r = serve.run_load(srv, pool, rate=rate, duration=args.serve_seconds, seed=int(rate))
-        b = serve.run_one_at_a_time(pool, rate=rate, duration=args.serve_seconds, seed=int(rate), device=dev)
-        out["loads"].append({"offered_req_s": rate, "server": r, "one_at_a_time": b})
+    progress(f"server: pool of {len(pool)} requests built")
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    out = {"workload": f"{len(pool)}-request pool, sizes log-uniform 4 KB..256 MB, FP64/FP32 50/50, "
+                       f"50/50 compress/decompress, Poisson arrivals, {args.serve_seconds:g} s per load",
+           "budget_bytes": 64 << 30, "loads": []}
+    with serve.Server(budget_bytes=64 << 30, host_budget_bytes=16 << 30, device=dev) as srv:
+        serve.run_load(srv, pool, rate=500, duration=0.3, seed=99)              # warm-up
+        for rate in rates:
+            out["loads"].append({"offered_req_s": rate,
+                                 "server": serve.run_load(srv, pool, rate=rate, duration=args.serve_seconds,
+                                                          seed=int(rate))})
+            progress(f"server: {rate:g} req/s done")
+    serve.run_one_at_a_time(pool, rate=500, duration=0.3, seed=99, device=dev)   # warm-up
+    for ld in out["loads"]:
+        rate = ld["offered_req_s"]
+        ld["one_at_a_time"] = serve.run_one_at_a_time(pool, rate=rate, duration=args.serve_seconds, seed=int(rate),
+                                                      device=dev)
+        ld["gbs_vs_one_at_a_time"] = ld["server"]["gbs"] / ld["one_at_a_time"]["gbs"]
+        progress(f"one at a time: {rate:g} req/s done")
     return out
 
 
@@ -488,19 +530,27 @@ def bench_pipeline(falcon, synth, torch, dev, n):
     out = torch.empty(((n + (1 << 23) - 1) >> 23) * falcon.bound(1 << 23, falcon.F64, BLOCK), dtype=torch.uint8).pin_memory()
     back = torch.empty(n, dtype=torch.float64).pin_memory()
     setup_s = time.perf_counter() - t0
-    falcon.pipeline_compress(h[:1 << 24], block=BLOCK, frame_values=1 << 23, nstreams=16, out=out)   # warm-up
-    t0 = time.perf_counter()
+    # one untimed pass over the whole buffers (the first pass over fresh page-locked memory
+    # runs 2-3x slower), then the median of three timed passes per direction
     s, fb = falcon.pipeline_compress(h, block=BLOCK, frame_values=1 << 23, nstreams=16, out=out)
-    tc = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    y = falcon.pipeline_decompress(s, fb, nstreams=16, out=back)
-    td = time.perf_counter() - t0
+    falcon.pipeline_decompress(s, fb, nstreams=16, out=back)
+    tcs, tds = [], []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        s, fb = falcon.pipeline_compress(h, block=BLOCK, frame_values=1 << 23, nstreams=16, out=out)
+        tcs.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        y = falcon.pipeline_decompress(s, fb, nstreams=16, out=back)
+        tds.append(time.perf_counter() - t0)
+    tc, td = statistics.median(tcs), statistics.median(tds)
     ok = bool(torch.equal(y.view(torch.int64), h.view(torch.int64)))
     link = host_link(torch, dev)
     nbytes = n * 8
     return {"workload": f"{n} FP64 values ({nbytes / 2**30:.1f} GiB) in pinned host memory, random walk, "
                         "3 places, 0.5% outliers; 64 MiB frames, 16 streams",
             "compress_gbs": nbytes / tc / 1e9, "decompress_gbs": nbytes / td / 1e9, "ratio": s.numel() / nbytes,
+            "compress_gbs_samples": [round(nbytes / t / 1e9, 1) for t in tcs],
+            "decompress_gbs_samples": [round(nbytes / t / 1e9, 1) for t in tds],
             "frames": len(fb), "bit_exact": ok, "host_link_gbs": link,
             "compress_frac_of_h2d": nbytes / tc / 1e9 / link["h2d"],
             "decompress_frac_of_d2h": nbytes / td / 1e9 / link["d2h"], "setup_s": setup_s}

@@ -167,8 +167,10 @@ int falcon_batch_forget(void *d_workspace);
  * payload copy ("P-D2H") of frame f overlaps the upload and compression of later frames and
  * the output needs no merging pass.  Every frame is a complete stream; the frames are
  * concatenated in h_out.  Host buffers should be page-locked (cudaHostAlloc) for the copies
- * to overlap; pageable memory works but serialises them.  The device buffers are allocated
- * per call (nstreams x (frame input + frame bound + workspace)) and freed before returning.
+ * to overlap; pageable memory works but serialises them.  The device buffers
+ * (nstreams x (frame input + frame bound + workspace)) are allocated on first use, kept per
+ * device for later calls (grown when a call needs more) and freed by falcon_release().
+ * Calls on the same device run one at a time.
  * ------------------------------------------------------------------------------------- */
 
 /* Compresses n values at h_in.  h_frame_bytes (host, ceil(n / frame_values) entries)
@@ -183,6 +185,87 @@ int falcon_pipeline_compress(const void *h_in, uint64_t n, int dtype, uint32_t b
  * parallel (the pre-allocation scheduler of Sec. 4).  *n_out receives the value count. */
 int falcon_pipeline_decompress(const void *h_in, const uint64_t *h_frame_bytes, uint64_t nframes,
                                int nstreams, void *h_out, size_t out_capacity_bytes, uint64_t *n_out);
+
+/* ---------------------------------------------------------------------------------------
+ * Request server: continuous batching of independent compress / decompress requests whose
+ * inputs are in host memory.  The paper has no server (it compresses one stream per call);
+ * this is how the library serves a stream of requests of mixed size and direction.
+ *
+ * A server owns, for its lifetime, on one device:
+ *   - a device arena of device_budget_bytes.  Every request in flight holds one block of it
+ *     (its input, its output and its look-back / offset words).  Requests are admitted in
+ *     submission order, each only when its block fits, so the server's device memory never
+ *     exceeds the budget (the memory-budget admission);
+ *   - a page-locked host arena of host_budget_bytes that receives the outputs;
+ *   - a worker thread and CUDA streams (one per copy direction, compute_streams for kernels).
+ * Each pass of the worker admits what fits (at most max_batch requests per direction) and
+ * turns the admitted requests into ONE batched launch per direction (the persistent kernels
+ * of the batched form above).  Uploads, the launch and the read-back of the per-request
+ * results are enqueued with device-side event dependencies.  A decompression's output copy
+ * is enqueued with them (its size is in the header); a compression's output is copied once
+ * its stream length has come back.  Requests that arrive while a batch runs join the next
+ * batch.  Input buffers should be page-locked for the uploads to overlap.
+ * ------------------------------------------------------------------------------------- */
+typedef struct falcon_server falcon_server;
+
+typedef struct {
+    uint64_t tag;          /* the caller's tag from falcon_server_submit */
+    int32_t status;        /* falcon_status of the request */
+    int32_t op;            /* FALCON_COMPRESS or FALCON_DECOMPRESS */
+    const void *h_out;     /* status OK: the output in the server's page-locked host arena
+                              (compress: the stream; decompress: the values), valid until
+                              falcon_server_free_output(h_out) or falcon_server_destroy.
+                              NULL on error. */
+    uint64_t out_bytes;    /* bytes at h_out */
+    uint64_t values;       /* values in the series (either direction) */
+    double latency_s;      /* submit -> completion, seconds (host steady clock) */
+} falcon_completion;
+
+typedef struct {
+    uint64_t submitted, completed, failed;          /* requests */
+    uint64_t batches, multi_request_batches;        /* batched launches (> 1 request) */
+    uint64_t max_batch, max_in_flight;              /* requests per launch / admitted at once */
+    uint64_t device_capacity, device_in_use, device_peak;   /* device arena bytes */
+    uint64_t host_capacity, host_in_use, host_peak;         /* host arena bytes */
+} falcon_server_stats;
+
+/* Creates a server on CUDA device `device`: allocates both arenas (cudaMalloc and
+ * cudaHostAlloc of the budgets) and starts the worker.  compute_streams >= 1;
+ * 1 <= max_batch <= 65536.  *out receives the handle. */
+int falcon_server_create(int device, size_t device_budget_bytes, size_t host_budget_bytes,
+                         int compute_streams, int max_batch, falcon_server **out);
+
+/* Queues one request; thread-safe.
+ *   op = FALCON_COMPRESS:   h_in = count values of dtype, chunks of block_size values;
+ *   op = FALCON_DECOMPRESS: h_in = a stream of count bytes (dtype and block_size ignored).
+ * h_in must stay valid and unchanged until the request's completion has been polled.
+ * Returns FALCON_OK (exactly one completion with `tag` follows) or, with nothing queued:
+ * FALCON_ERR_INVALID (arguments, or the server is shutting down), FALCON_ERR_CORRUPT (the
+ * stream header is malformed), FALCON_ERR_UNSUPPORTED (block size), FALCON_ERR_CAPACITY (the
+ * request's device block or output can never fit the arenas), FALCON_ERR_CUDA (a CUDA call
+ * of the server failed earlier; the server accepts no more work). */
+int falcon_server_submit(falcon_server *server, int op, const void *h_in, uint64_t count,
+                         int dtype, uint32_t block_size, uint64_t tag);
+
+/* Moves up to max_completions finished requests into out[] (any order) and their number into
+ * *count, waiting up to timeout_us microseconds for the first one.  Thread-safe.  A request
+ * whose kernel found an error (e.g. a corrupt chunk-size array) completes with that status;
+ * requests still queued when the server is destroyed complete with FALCON_ERR_CAPACITY if
+ * the host arena never had room for them. */
+int falcon_server_poll(falcon_server *server, falcon_completion *out, int max_completions,
+                       int timeout_us, int *count);
+
+/* Returns an output (completion.h_out) to the host arena.  Outputs that are never returned
+ * keep their space, and admission waits for host-arena room. */
+int falcon_server_free_output(falcon_server *server, const void *h_out);
+
+/* Counters and arena occupancy (a snapshot). */
+int falcon_server_get_stats(falcon_server *server, falcon_server_stats *stats);
+
+/* Stops accepting requests, finishes every admitted and queued request, stops the worker
+ * and frees the arenas, streams and the handle.  Outputs not yet freed become invalid;
+ * completions not yet polled are dropped. */
+int falcon_server_destroy(falcon_server *server);
 
 /* Persistent-grid size: at most ctas_per_sm resident CTAs per SM for each direction
  * (0 = as many as fit).  Does not change any output byte; used by the autotuner. */

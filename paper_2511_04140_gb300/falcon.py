@@ -32,6 +32,20 @@ class Series(ctypes.Structure):
                 ("block_size", ctypes.c_uint32), ("h_header", ctypes.c_void_p)]
 
 
+class Completion(ctypes.Structure):
+    """falcon_completion (include/falcon.h)."""
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("h_out", ctypes.c_void_p), ("out_bytes", ctypes.c_uint64), ("values", ctypes.c_uint64),
+                ("latency_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    """falcon_server_stats (include/falcon.h)."""
+    _fields_ = [(k, ctypes.c_uint64) for k in (
+        "submitted", "completed", "failed", "batches", "multi_request_batches", "max_batch", "max_in_flight",
+        "device_capacity", "device_in_use", "device_peak", "host_capacity", "host_in_use", "host_peak")]
+
+
 class FalconError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -81,6 +95,18 @@ def _load():
             L.falcon_pipeline_compress.argtypes = [vp, u64, ci, u32, u64, ci, vp, sz, vp, c.POINTER(sz)]
             L.falcon_pipeline_decompress.restype = ci
             L.falcon_pipeline_decompress.argtypes = [vp, vp, u64, ci, vp, sz, c.POINTER(u64)]
+            L.falcon_server_create.restype = ci
+            L.falcon_server_create.argtypes = [ci, sz, sz, ci, ci, c.POINTER(vp)]
+            L.falcon_server_submit.restype = ci
+            L.falcon_server_submit.argtypes = [vp, ci, vp, u64, ci, u32, u64]
+            L.falcon_server_poll.restype = ci
+            L.falcon_server_poll.argtypes = [vp, c.POINTER(Completion), ci, ci, c.POINTER(ci)]
+            L.falcon_server_free_output.restype = ci
+            L.falcon_server_free_output.argtypes = [vp, vp]
+            L.falcon_server_get_stats.restype = ci
+            L.falcon_server_get_stats.argtypes = [vp, c.POINTER(ServerStats)]
+            L.falcon_server_destroy.restype = ci
+            L.falcon_server_destroy.argtypes = [vp]
             _lib = L
     return _lib
 

@@ -1,28 +1,29 @@
-"""Continuous-batching compression server on one GPU.
+"""Continuous-batching compression server on one GPU (Python face of falcon_server_*).
 
-Requests (compress a host array, or decompress a host stream) are admitted in arrival order
-while the device-memory budget allows, so new requests join while earlier ones are still on
-the GPU.  The scheduler thread loops over four stages without blocking on any of them:
+The scheduler is native (the library's worker thread, see include/falcon.h):
+  - admission in arrival order against a device-memory budget: every request in flight
+    holds one block of a device arena of that size (input, output, look-back words), and
+    its output one block of a page-locked host arena;
+  - each pass of the worker turns everything admitted into ONE batched persistent launch per
+    direction, with the uploads, the launch, the per-request result read-back (the paper's
+    M-D2H) and, for decompression, the output copy (P-D2H) chained by device-side events;
+    compression outputs are copied once their lengths are back.  Requests that arrive while
+    a batch runs join the next one.
+This module adds futures: a poller thread drains completions (the ctypes call releases the
+GIL while it waits) and resolves each request's Future with a zero-copy tensor over the
+host arena, whose space returns to the arena when the tensor is garbage collected.
 
-  1. admit   - reserve device memory for input, output and workspace, copy the input
-               host -> device on the upload stream (pinned payloads overlap fully);
-  2. launch  - every admitted request whose upload finished joins ONE batched launch per
-               direction (falcon_batch_plan + falcon_batch_launch) on one of several compute
-               streams, so batches overlap each other and the copies;
-  3. size    - for compression, the per-series results (stream length, status) come back
-               with a 16-byte-per-request copy (the paper's M-D2H);
-  4. return  - the payload goes device -> host (P-D2H) into a pinned buffer; when that copy
-               completes the request's future resolves and its memory budget is released.
-
-Latency = time from submit() to the resolved future.  Every result is byte-identical to
-the same request processed alone (the codec is deterministic and per-series).
+Latency = time from submit() to completion, measured by the library.  Every result is
+byte-identical to the same request processed alone (the codec is deterministic and
+per-series).
 """
 from __future__ import annotations
 
-import collections
 import concurrent.futures as cf
+import ctypes
 import threading
 import time
+import weakref
 
 import numpy as np
 import torch
@@ -30,69 +31,83 @@ import torch
 from . import falcon
 
 COMPRESS, DECOMPRESS = "compress", "decompress"
-
-
-class _Req:
-    __slots__ = ("op", "payload", "block", "future", "t_submit", "t_done", "need", "d_in", "d_out", "nbytes",
-                 "header", "ev", "host_out", "n", "dtype_code", "stage", "batch", "index")
-
-    def __init__(self, op, payload, block):
-        self.op = op
-        self.payload = payload
-        self.block = block
-        self.future = cf.Future()
-        self.t_submit = time.perf_counter()
-        self.t_done = None
-        self.stage = "queued"
+_OPS = {COMPRESS: falcon.COMPRESS, DECOMPRESS: falcon.DECOMPRESS}
 
 
 class Server:
-    """Continuous-batching server.
+    """Server(budget_bytes=64 << 30).submit("compress", host_values)    -> Future[uint8 tensor]
+    Server.submit("decompress", host_uint8_stream)                       -> Future[value tensor]
 
-    Server(budget_bytes=64 << 30).submit("compress", host_tensor) -> Future[uint8 host tensor]
-    Server.submit("decompress", host_uint8_tensor)                  -> Future[value host tensor]
-    """
+    Results are views of the server's page-locked output arena, valid until close(); clone()
+    what must outlive the server.  Inputs must stay unchanged until their future resolves
+    (the server keeps a reference).  Futures carry `.latency` (seconds)."""
 
-    def __init__(self, budget_bytes: int = 64 << 30, device="cuda", block: int = 1024,
-                 compute_streams: int = 4, max_batch: int = 1024, idle_sleep: float = 20e-6):
+    def __init__(self, budget_bytes: int = 64 << 30, host_budget_bytes: int = 16 << 30, device="cuda",
+                 block: int = 1024, compute_streams: int = 4, max_batch: int = 1024):
         self.device = torch.device(device)
-        self.budget = budget_bytes
+        index = self.device.index if self.device.index is not None else torch.cuda.current_device()
         self.block = block
-        self.max_batch = max_batch
-        self.idle_sleep = idle_sleep
-        self.in_use = 0
-        self._pending = collections.deque()
+        self._L = falcon.lib()
+        h = ctypes.c_void_p()
+        falcon._check(self._L.falcon_server_create(index, budget_bytes, host_budget_bytes, compute_streams,
+                                                   max_batch, ctypes.byref(h)), "server_create")
+        self._h = h.value
         self._lock = threading.Lock()
-        self._cv = threading.Condition(self._lock)
-        self._running = True
-        self.stats = {"batches": 0, "requests": 0, "max_batch": 0, "multi_request_batches": 0,
-                      "max_in_flight": 0}
-        with torch.cuda.device(self.device):
-            self.up = torch.cuda.Stream(self.device)
-            self.down = torch.cuda.Stream(self.device)
-            self.plan_stream = torch.cuda.Stream(self.device)
-            self.compute = [torch.cuda.Stream(self.device) for _ in range(compute_streams)]
-        self._next_compute = 0
-        self._thread = threading.Thread(target=self._loop, name="falcon-server", daemon=True)
-        self._thread.start()
+        self._futs: dict = {}
+        self._tag = 0
+        self._open = True
+        self._closing = False
+        self._poller = threading.Thread(target=self._poll_loop, name="falcon-server-poll", daemon=True)
+        self._poller.start()
 
     # ------------------------------------------------------------------ public API
     def submit(self, op: str, payload: torch.Tensor, block: int | None = None) -> cf.Future:
-        if op not in (COMPRESS, DECOMPRESS):
+        if op not in _OPS:
             raise ValueError(op)
         if payload.is_cuda:
             raise ValueError("payload must be a host tensor")
-        r = _Req(op, payload.contiguous(), block or self.block)
-        with self._cv:
-            self._pending.append(r)
-            self._cv.notify()
-        return r.future
+        payload = payload.contiguous()
+        if op == COMPRESS:
+            code, count = falcon._dtype_code(payload), payload.numel()
+        else:
+            if payload.dtype != torch.uint8:
+                raise TypeError("a stream is a uint8 tensor")
+            code, count = 0, payload.numel()
+        f = cf.Future()
+        with self._lock:
+            if self._closing:
+                raise RuntimeError("server is closed")
+            tag = self._tag
+            self._tag += 1
+            self._futs[tag] = (f, payload)
+        st = self._L.falcon_server_submit(self._h, _OPS[op], payload.data_ptr(), count, code, block or self.block, tag)
+        if st != falcon.OK:
+            with self._lock:
+                self._futs.pop(tag, None)
+            f.set_exception(falcon.FalconError(st, f"server {op}"))
+        return f
+
+    @property
+    def stats(self) -> dict:
+        s = falcon.ServerStats()
+        falcon._check(self._L.falcon_server_get_stats(self._h, ctypes.byref(s)), "server_get_stats")
+        d = {k: getattr(s, k) for k, _ in falcon.ServerStats._fields_}
+        d["requests"] = d["submitted"]
+        return d
+
+    @property
+    def in_use(self) -> int:
+        return self.stats["device_in_use"]
 
     def close(self) -> None:
-        with self._cv:
-            self._running = False
-            self._cv.notify()
-        self._thread.join()
+        with self._lock:
+            if self._closing:
+                return
+            self._closing = True
+        self._poller.join()
+        with self._lock:
+            self._open = False
+        falcon._check(self._L.falcon_server_destroy(self._h), "server_destroy")
 
     def __enter__(self):
         return self
@@ -100,139 +115,92 @@ class Server:
     def __exit__(self, *exc):
         self.close()
 
-    # ------------------------------------------------------------------ scheduler
-    def _need(self, r: _Req) -> int:
-        if r.op == COMPRESS:
-            x = r.payload
-            code = falcon._dtype_code(x)
-            nc = (x.numel() + r.block - 1) // r.block
-            return x.numel() * x.element_size() + falcon.bound(x.numel(), code, r.block) + falcon.workspace_bytes(nc) + 4096
-        hdr = r.payload[:falcon.HEADER_BYTES].numpy().tobytes()
-        n, code, blk, nc = falcon.stream_info(hdr)
-        return r.payload.numel() + n * (8 if code == falcon.F64 else 4) + falcon.workspace_bytes(nc) + 4096
+    # ------------------------------------------------------------------ completions
+    def _free(self, ptr: int) -> None:
+        with self._lock:
+            if self._open:
+                self._L.falcon_server_free_output(self._h, ptr)
 
-    def _fail(self, r: _Req, exc: Exception) -> None:
-        self.in_use -= getattr(r, "need", 0) or 0
-        r.t_done = time.perf_counter()
-        if not r.future.done():
-            r.future.set_exception(exc)
+    def _wrap(self, c, payload) -> torch.Tensor:
+        nbytes = int(c.out_bytes)
+        if c.op == falcon.COMPRESS:
+            dtype = torch.uint8
+        else:
+            es = nbytes // c.values if c.values else (8 if int(payload[5]) == falcon.F64 else 4)
+            dtype = torch.float64 if es == 8 else torch.float32
+        raw = (ctypes.c_uint8 * nbytes).from_address(c.h_out) if nbytes else bytearray(0)
+        arr = np.frombuffer(raw, dtype=np.uint8)
+        weakref.finalize(arr, self._free, c.h_out)        # arena space back when unreferenced
+        t = torch.from_numpy(arr)
+        return t if dtype == torch.uint8 else t.view(dtype)
 
-    def _admit(self, admitted: list) -> None:
+    def _poll_loop(self) -> None:
+        buf = (falcon.Completion * 256)()
+        cnt = ctypes.c_int()
         while True:
-            with self._lock:
-                if not self._pending:
-                    return
-                r = self._pending[0]
-                try:
-                    need = self._need(r)
-                except Exception as exc:                     # malformed request: reject it
-                    self._pending.popleft()
-                    self._fail(r, exc)
-                    continue
-                if self.in_use + need > self.budget and self.in_use > 0:
-                    return                                   # wait for memory to free up
-                self._pending.popleft()
-            r.need = need
-            self.in_use += need
-            with torch.cuda.stream(self.up):
-                if r.op == COMPRESS:
-                    r.d_in = r.payload.to(self.device, non_blocking=True)
+            falcon._check(self._L.falcon_server_poll(self._h, buf, 256, 20000, ctypes.byref(cnt)), "server_poll")
+            for i in range(cnt.value):
+                c = buf[i]
+                with self._lock:
+                    f, payload = self._futs.pop(c.tag)
+                f.latency = c.latency_s
+                if c.status != falcon.OK:
+                    f.set_exception(falcon.FalconError(c.status, "server request"))
                 else:
-                    r.header = r.payload[:falcon.HEADER_BYTES].numpy().tobytes()
-                    r.n, r.dtype_code, _, _ = falcon.stream_info(r.header)
-                    r.d_in = torch.empty(((r.payload.numel() + 15) // 16) * 16, dtype=torch.uint8, device=self.device)
-                    r.d_in[:r.payload.numel()].copy_(r.payload, non_blocking=True)
-                r.ev = torch.cuda.Event()
-                r.ev.record(self.up)
-            r.stage = "uploading"
-            admitted.append(r)
-            self.stats["max_in_flight"] = max(self.stats["max_in_flight"], len(admitted))
+                    f.set_result(self._wrap(c, payload))
+                del f, payload                 # hold no output here: its space must return
+            with self._lock:
+                if self._closing and not self._futs:
+                    return
 
-    def _launch_ready(self, admitted: list) -> None:
-        ready = [r for r in admitted if r.stage == "uploading" and r.ev.query()]
-        for op in (COMPRESS, DECOMPRESS):
-            group = [r for r in ready if r.op == op][:self.max_batch]
-            if not group:
-                continue
-            st = self.compute[self._next_compute % len(self.compute)]
-            self._next_compute += 1
-            try:
-                with torch.cuda.stream(self.plan_stream):
-                    if op == COMPRESS:
-                        b = falcon.Batch(falcon.COMPRESS, [r.d_in for r in group], block=group[0].block
-                                         if len({r.block for r in group}) == 1 else self.block, device=self.device)
-                    else:
-                        b = falcon.Batch(falcon.DECOMPRESS, [(r.d_in, r.payload.numel(), r.header) for r in group],
-                                         device=self.device)
-                st.wait_stream(self.up)
-                b.launch(st)
-            except Exception as exc:
-                for r in group:
-                    admitted.remove(r)
-                    self._fail(r, exc)
-                continue
-            ev = torch.cuda.Event()
-            ev.record(st)
-            for i, r in enumerate(group):
-                r.batch, r.index, r.stage, r.ev = b, i, "computing", ev
-            self.stats["batches"] += 1
-            self.stats["requests"] += len(group)
-            self.stats["max_batch"] = max(self.stats["max_batch"], len(group))
-            self.stats["multi_request_batches"] += len(group) > 1
 
-    def _collect(self, admitted: list) -> None:
-        for r in list(admitted):
-            if r.stage == "computing" and r.ev.query():
-                b = r.batch
-                if not hasattr(b, "_res"):
-                    with torch.cuda.stream(self.plan_stream):
-                        b._res = b.results()                 # 16 bytes per request (M-D2H)
-                nb, status = b._res[r.index]
-                if status != 0:
-                    admitted.remove(r)
-                    self._fail(r, falcon.FalconError(status, r.op))
-                    continue
-                out = b.outputs[r.index]
-                with torch.cuda.stream(self.down):
-                    self.down.wait_event(r.ev)
-                    if r.op == COMPRESS:
-                        r.host_out = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
-                        r.host_out.copy_(out[:nb], non_blocking=True)
-                    else:
-                        r.host_out = torch.empty(nb, dtype=out.dtype, pin_memory=True)
-                        r.host_out.copy_(out[:nb], non_blocking=True)
-                    r.ev = torch.cuda.Event()
-                    r.ev.record(self.down)
-                r.stage = "returning"
-            elif r.stage == "returning" and r.ev.query():
-                admitted.remove(r)
-                self.in_use -= r.need
-                r.t_done = time.perf_counter()
-                r.d_in = None
-                r.batch = None
-                r.future.latency = r.t_done - r.t_submit
-                r.future.set_result(r.host_out)
+def _bytes_of(op, payload, out):
+    return payload.numel() * payload.element_size() if op == COMPRESS else out.numel() * out.element_size()
 
-    def _loop(self) -> None:
-        admitted: list = []
-        with torch.cuda.device(self.device):
-            while True:
-                with self._cv:
-                    if not self._running and not self._pending and not admitted:
-                        break
-                    if not self._pending and not admitted:
-                        self._cv.wait(timeout=0.05)
-                        continue
-                try:
-                    self._admit(admitted)
-                    self._launch_ready(admitted)
-                    self._collect(admitted)
-                except Exception as exc:                     # keep serving; fail what is in flight
-                    for r in list(admitted):
-                        admitted.remove(r)
-                        self._fail(r, exc)
-                if admitted:
-                    time.sleep(self.idle_sleep)
+
+def run_load(server: Server, pool, rate: float, duration: float, seed: int = 0) -> dict:
+    """Poisson arrivals at `rate` requests/s for `duration` seconds; each request is drawn
+    uniformly from `pool` (list of (op, host tensor)).  Throughput counts original
+    (uncompressed) bytes; latency runs from the scheduled arrival to the moment the client
+    sees the result (as in run_one_at_a_time)."""
+    arr = _arrivals(rate, duration, len(pool), seed)
+    lock = threading.Lock()
+    acc = {"bytes": 0, "done": 0, "failed": 0}
+    lat: list = []
+    all_done = threading.Event()
+
+    def record(f, op, payload, t_arrival):
+        # the client keeps only latency and byte counts; the output returns to the arena
+        t_seen = time.perf_counter() - t0
+        with lock:
+            if f.exception() is None:
+                lat.append(t_seen - t_arrival)
+                acc["bytes"] += _bytes_of(op, payload, f.result())
+            else:
+                acc["failed"] += 1
+            acc["done"] += 1
+            if acc["done"] == len(arr):
+                all_done.set()
+
+    before = server.stats
+    t0 = time.perf_counter()
+    for t, i in arr:
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        op, payload = pool[i]
+        server.submit(op, payload).add_done_callback(lambda f, op=op, p=payload, t=t: record(f, op, p, t))
+    if arr:
+        all_done.wait()
+    wall = time.perf_counter() - t0
+    after = server.stats
+    res = _summary(lat, acc["bytes"], wall, len(arr))
+    res["failed"] = acc["failed"]
+    res["batches"] = after["batches"] - before["batches"]
+    res["multi_request_batches"] = after["multi_request_batches"] - before["multi_request_batches"]
+    res["mean_batch"] = len(arr) / max(1, res["batches"])
+    res.update({k: after[k] for k in ("max_batch", "max_in_flight", "device_peak")})
+    return res
 
 
 def _arrivals(rate: float, duration: float, npool: int, seed: int):
@@ -249,34 +217,6 @@ def _summary(lat, nbytes, wall, n):
     lat = sorted(lat)
     q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] * 1e3 if lat else None
     return {"requests": n, "p50_ms": q(0.5), "p99_ms": q(0.99), "gbs": nbytes / wall / 1e9, "wall_s": wall}
-
-
-def _bytes_of(op, payload, out):
-    return payload.numel() * payload.element_size() if op == COMPRESS else out.numel() * out.element_size()
-
-
-def run_load(server: Server, pool, rate: float, duration: float, seed: int = 0) -> dict:
-    """Poisson arrivals at `rate` requests/s for `duration` seconds; each request is drawn
-    uniformly from `pool` (list of (op, host tensor)).  Throughput counts original
-    (uncompressed) bytes; latency runs from arrival to the resolved future."""
-    arr = _arrivals(rate, duration, len(pool), seed)
-    futs = []
-    t0 = time.perf_counter()
-    for t, i in arr:
-        now = time.perf_counter() - t0
-        if t > now:
-            time.sleep(t - now)
-        op, payload = pool[i]
-        futs.append((server.submit(op, payload), op, payload))
-    nbytes, lat = 0, []
-    for f, op, payload in futs:
-        out = f.result()
-        lat.append(f.latency)
-        nbytes += _bytes_of(op, payload, out)
-    wall = time.perf_counter() - t0
-    res = _summary(lat, nbytes, wall, len(futs))
-    res.update({k: server.stats[k] for k in ("batches", "max_batch", "multi_request_batches", "max_in_flight")})
-    return res
 
 
 def run_one_at_a_time(pool, rate: float, duration: float, seed: int = 0, device="cuda", block: int = 1024) -> dict:
