@@ -116,6 +116,23 @@ int falcon_decompress_async(const void *d_in, size_t in_bytes, const void *h_hea
                             void *d_out, size_t out_capacity_bytes, void *d_workspace,
                             size_t workspace_bytes, uint64_t *d_result, void *stream);
 
+/* Allocation-free compression.  The paper has no counterpart: it is a deployment variant of
+ * falcon_compress_async whose look-back scratch (control block and look-back words) is a
+ * file-scope static device array of the library, sized for FALCON_NOALLOC_MAX_CHUNKS chunks
+ * (540,928 bytes per device; 67,108,864 values at block_size 1024), instead of a workspace.
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *   - The first call on a device looks the array's address up (cudaGetSymbolAddress, with
+ *     that device current) and keeps it; make that first call before any stream capture.
+ *   - Zeroes, on `stream`, the scratch words it uses and d_result before the kernel.
+ *   - Every call on a device uses the same array: calls that overlap in time (two streams,
+ *     or two host threads without ordering) race and corrupt each other's output; order
+ *     them on one stream.
+ *   - More than FALCON_NOALLOC_MAX_CHUNKS chunks: FALCON_ERR_UNSUPPORTED, nothing enqueued.
+ * Arguments, d_result and the other errors are those of falcon_compress_async. */
+#define FALCON_NOALLOC_MAX_CHUNKS 65536
+int falcon_compress_noalloc(const void *d_in, uint64_t n, int dtype, uint32_t block_size,
+                            void *d_out, size_t out_capacity, uint64_t *d_result, void *stream);
+
 /* Frees the workspaces cached by falcon_compress / falcon_decompress on every device. */
 int falcon_release(void);
 

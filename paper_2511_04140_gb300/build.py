@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfalcon.so")
-SOURCES = ["capi.cu", "compress.cu", "decompress.cu", "pipeline.cu", "server.cu"]
+SOURCES = ["capi.cu", "compress.cu", "decompress.cu", "pipeline.cu", "server.cu", "noalloc.cu"]
 HEADERS = ["falcon_device.cuh", "falcon_internal.h", "falcon_tables.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -95,6 +95,8 @@ def _load():
             L.falcon_pipeline_compress.argtypes = [vp, u64, ci, u32, u64, ci, vp, sz, vp, c.POINTER(sz)]
             L.falcon_pipeline_decompress.restype = ci
             L.falcon_pipeline_decompress.argtypes = [vp, vp, u64, ci, vp, sz, c.POINTER(u64)]
+            L.falcon_compress_noalloc.restype = ci
+            L.falcon_compress_noalloc.argtypes = [vp, u64, ci, u32, vp, sz, vp, vp]
             L.falcon_server_create.restype = ci
             L.falcon_server_create.argtypes = [ci, sz, sz, ci, ci, c.POINTER(vp)]
             L.falcon_server_submit.restype = ci
@@ -201,6 +203,12 @@ def decompress_async(s: torch.Tensor, nbytes: int, header: bytes, out: torch.Ten
                                            out.numel() * out.element_size(), workspace.data_ptr(),
                                            workspace.numel(), result.data_ptr(), _stream_ptr(stream)),
            "decompress_async")
+
+
+def compress_noalloc(x: torch.Tensor, block: int, out: torch.Tensor, result: torch.Tensor, stream=None) -> None:
+    """falcon_compress_noalloc: as compress_async, with the library's static scratch."""
+    _check(_load().falcon_compress_noalloc(x.data_ptr(), x.numel(), _dtype_code(x), block, out.data_ptr(),
+                                           out.numel(), result.data_ptr(), _stream_ptr(stream)), "compress_noalloc")
 
 
 def release() -> None:
