@@ -9,8 +9,9 @@
  *     verified to round-trip bit for bit; otherwise Case 2 g_i = Zigzag(BinLong(v_i)));
  *   - delta + zigzag coding (Eq. 5);
  *   - the adaptive sparse/dense bit-plane encoding of Sec. 3.3 (Fig. 8);
- *   - the compressed-size synchronisation and chunk writing of Sec. 3.4 (Alg. 3), as a
- *     single-pass decoupled look-back inside the kernel;
+ *   - the compressed-size synchronisation and chunk writing of Sec. 3.4 (Alg. 3): the record
+ *     sizes, their exclusive prefix per stream, then every record written at its offset
+ *     (three kernel launches on the caller's stream, none waiting on another warp);
  * and decompression (Sec. 4) is its exact inverse.  FP32 follows the same steps with
  * alpha <= 10, beta <= 7 and 32-bit integers.
  *
@@ -99,7 +100,7 @@ int falcon_decompress(const void *d_in, size_t in_bytes, void *d_out, size_t out
  * num_chunks chunks.  Must be 256-byte aligned device memory. */
 size_t falcon_workspace_bytes(uint64_t num_chunks);
 
-/* Asynchronous compression: enqueues a workspace reset and the kernel on `stream` and
+/* Asynchronous compression: enqueues a workspace reset and the kernels on `stream` and
  * returns without synchronising, so it can be captured in a CUDA graph.
  * d_result (device, 2 x uint64): [0] = stream length in bytes, [1] = falcon_status of the
  * device-side work (the host return value only covers argument checks and launch).
@@ -117,13 +118,13 @@ int falcon_decompress_async(const void *d_in, size_t in_bytes, const void *h_hea
                             size_t workspace_bytes, uint64_t *d_result, void *stream);
 
 /* Allocation-free compression.  The paper has no counterpart: it is a deployment variant of
- * falcon_compress_async whose look-back scratch (control block and look-back words) is a
- * file-scope static device array of the library, sized for FALCON_NOALLOC_MAX_CHUNKS chunks
- * (540,928 bytes per device; 67,108,864 values at block_size 1024), instead of a workspace.
+ * falcon_compress_async whose scratch (control block and per-chunk words) is a file-scope
+ * static device array of the library, sized for FALCON_NOALLOC_MAX_CHUNKS chunks
+ * (1,048,832 bytes per device; 67,108,864 values at block_size 1024), instead of a workspace.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  *   - The first call on a device looks the array's address up (cudaGetSymbolAddress, with
  *     that device current) and keeps it; make that first call before any stream capture.
- *   - Zeroes, on `stream`, the scratch words it uses and d_result before the kernel.
+ *   - Zeroes, on `stream`, the scratch words it uses and d_result before the kernels.
  *   - Every call on a device uses the same array: calls that overlap in time (two streams,
  *     or two host threads without ordering) race and corrupt each other's output; order
  *     them on one stream.
@@ -156,11 +157,11 @@ typedef struct {
     const void *h_header;   /* decompress: HOST copy of the stream's first 32 bytes; compress: NULL */
 } falcon_series;
 
-/* Device workspace (bytes) a batch plan of `count` series needs (job table + look-back
+/* Device workspace (bytes) a batch plan of `count` series needs (job table + per-chunk
  * words).  Returns 0 if a series is invalid. */
 size_t falcon_batch_workspace_bytes(int direction, const falcon_series *h_series, int count);
 
-/* Validates the series, lays out the job table and look-back words in d_workspace (256-byte
+/* Validates the series, lays out the job table and per-chunk words in d_workspace (256-byte
  * aligned device memory of workspace_bytes) and uploads the table with a copy enqueued on
  * `stream`.  d_results (device, 2 * count uint64): after each launch [2i] = stream bytes
  * (compress) or values (decompress) of series i and [2i+1] = its falcon_status.
@@ -210,7 +211,7 @@ int falcon_pipeline_decompress(const void *h_in, const uint64_t *h_frame_bytes, 
  *
  * A server owns, for its lifetime, on one device:
  *   - a device arena of device_budget_bytes.  Every request in flight holds one block of it
- *     (its input, its output and its look-back / offset words).  Requests are admitted in
+ *     (its input, its output and its per-chunk workspace words).  Requests are admitted in
  *     submission order, each only when its block fits, so the server's device memory never
  *     exceeds the budget (the memory-budget admission);
  *   - a page-locked host arena of host_budget_bytes that receives the outputs;

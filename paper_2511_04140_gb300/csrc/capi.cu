@@ -193,7 +193,7 @@ int falcon_stream_info(const void *h_header, size_t len, uint64_t *n, int *dtype
 }
 
 size_t falcon_workspace_bytes(uint64_t nchunks) {
-    const size_t words = (size_t)(nchunks + (nchunks + 31) / 32);
+    const size_t words = (size_t)workspace_words(nchunks);
     return kControlBytes + ((8 * words + 255) / 256) * 256;
 }
 
@@ -316,7 +316,7 @@ struct BatchPlan {
     int direction;
     int count;
     uint64_t total_chunks;
-    size_t reset_bytes;       // control block + look-back words, zeroed before each launch
+    size_t reset_bytes;       // control block + workspace words, zeroed before each launch
     uint64_t *d_results;
 };
 std::mutex g_plan_mu;
@@ -351,9 +351,9 @@ int build_jobs(int direction, const falcon_series *series, int count, std::vecto
         }
         j.chunk_begin = total_chunks;
         total_chunks += j.nchunks;
-        // look-back words (compress) / chunk offsets (decompress), 8-byte each
+        // per-chunk workspace words, 8-byte each
         j.flags = reinterpret_cast<unsigned long long *>((uintptr_t)words);   // offset, fixed up later
-        words += (size_t)(j.nchunks + (j.nchunks + 31) / 32);
+        words += (size_t)workspace_words(j.nchunks);
         jobs[(size_t)i] = j;
     }
     return FALCON_OK;
@@ -410,7 +410,7 @@ int falcon_batch_launch(void *d_workspace, void *stream) {
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     uint8_t *w8 = static_cast<uint8_t *>(d_workspace);
-    // the control block and the look-back words; the job table in between is kept
+    // the control block and the workspace words; the job table in between is kept
     const size_t table = align256(sizeof(Job) * (size_t)plan.count);
     if (cudaMemsetAsync(w8, 0, kControlBytes, s) != cudaSuccess) return FALCON_ERR_CUDA;
     if (plan.reset_bytes > kControlBytes + table &&

@@ -1,19 +1,24 @@
-// Falcon compression kernel (Sec. 3 of the paper; Alg. 3 CmpKernel) for sm_103a.
-//
-// One persistent launch; each warp repeatedly claims a chunk (dynamic ticket, so that the
-// decoupled look-back only waits on chunks owned by running warps).  While it works on one
-// chunk, the next chunk's values are already streaming into its second shared-memory buffer
-// (cp.async, swizzled).  Per chunk:
-//   1. read the lane's 32 values, classify (R1 specials) and take the chunk maximum,
-//   2. Case 1 / Case 2 of Eq. 4: the smallest decimal place alpha_max at which every value
-//      passes Alg. 2's test, in exact integer arithmetic (q_test); FP32 follows Alg. 2 value
-//      by value,
-//   3. G (Eq. 4), Z (Eq. 5) and the bit width w in registers,
-//   4. 32x32 register transposes give one 32-bit word per bit plane (4 row bytes per lane);
-//      the words go to shared memory and their non-zero bytes are counted (Sec. 3.3 lambda),
-//   5. sparse/dense per row -> record size -> decoupled look-back (Sec. 3.4) -> offset,
-//   6. the record is assembled in shared memory at the output's 16-byte phase, in place of
-//      the plane words it consumes, and written with aligned 16-byte stores.
+// Falcon compression (Sec. 3 of the paper; the work of Alg. 3 CmpKernel) for sm_103a, as
+// three launches, none of which waits on another warp:
+//   1. analyse: each warp takes chunks in a fixed stride (the next chunk's values already
+//      streaming into its second shared-memory buffer, cp.async, swizzled) and computes
+//      - the lane's 32 values, specials (R1) and the chunk maximum,
+//      - Case 1 / Case 2 of Eq. 4: the smallest decimal place alpha_max at which every value
+//        passes Alg. 2's test, in exact integer arithmetic (q_test); FP32 follows Alg. 2
+//        value by value,
+//      - G (Eq. 4), Z (Eq. 5) and the bit width w in registers,
+//      - 32x32 register transposes (one 32-bit word per bit plane: 4 row bytes per lane) and
+//        the non-zero bytes of every row (Sec. 3.3 lambda), sparse/dense per row, the record
+//        size, which goes into the stream's size array, and alpha, beta_hat, w and the
+//        dense-row mask, which go into the workspace;
+//   2. offsets: the exclusive prefix of each job's size array (the size synchronisation of
+//      Sec. 3.4), the stream header and length and the capacity check;
+//   3. emit: G, Z and the bit planes again from the kept alpha and w, the record assembled in
+//      shared memory at the output's 16-byte phase, in place of the plane words it consumes,
+//      and written with aligned 16-byte stores at its offset.
+// The paper resolves offsets inside one launch with a decoupled look-back; with about 1800
+// resident warps on a GB300 the waits of that look-back took half of every warp's time, while
+// the analysis recomputed by the emit launch costs less.
 #include "falcon_device.cuh"
 
 namespace falcon {
@@ -172,32 +177,69 @@ __device__ __forceinline__ void issue_chunk(const Job *jobs, int njobs, const Jo
     else stage_values_async<false>(job.in + first * 4u, m, buf, lane);
 }
 
-// A chunk whose size is published and whose record waits for its offset.
-struct Pend {
-    uint64_t t;             // global ticket
-    uint64_t z1;
-    uint64_t dense_mask;
-    uint32_t size;
-    int w;
-    int alpha_byte;         // header byte 0 (alpha_max or the Case-2 sentinel)
-    int beta_hat;           // header byte 1
-    bool valid;
-};
+// Workspace words of a job (job.flags), written by the analysis launch:
+//   flags[c]            bits 47..63: alpha byte (5 bits) | beta_hat (5) | w (7); the offsets
+//                       launch adds the chunk's exclusive offset in bits 0..46;
+//   flags[nchunks + c]  the dense-row mask (bit p: plane p is stored dense).
+constexpr int kMetaShift = 47;
+constexpr unsigned long long kOffMask = (1ull << kMetaShift) - 1ull;
 
-// Steps 1-5: everything up to the record size, which is published for the look-back.
-// The plane words stay in buf for finish_chunk.
+__device__ __forceinline__ unsigned long long pack_meta(int alpha_byte, int beta_hat, int w) {
+    return (unsigned long long)(((uint32_t)alpha_byte << 12) | ((uint32_t)beta_hat << 7) | (uint32_t)w) << kMetaShift;
+}
+
+// G (Eq. 4) and Z (Eq. 5) in place: v[k] becomes Z of column 32 lane + k, pad columns (R11)
+// are zero; alpha < 0 means Case 2.  Returns z_1 (every lane) and the OR of the lane's Z.
 template <bool F64>
-__device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t *scratch, int lane,
-                              int &hint, Pend &pd) {
-    const uint64_t c = t - job.chunk_begin;
+__device__ __forceinline__ typename Traits<F64>::U to_z(typename Traits<F64>::U (&v)[32],
+                                                        typename Traits<F64>::U vx, int alpha, uint32_t m,
+                                                        int lane, typename Traits<F64>::U &zor) {
+    using U = typename Traits<F64>::U;
+    U gx;
+    if (alpha >= 0) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = case1_g(v[k], alpha);
+        gx = case1_g(vx, alpha);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) v[k] = zigzag(v[k]);
+        gx = zigzag(vx);
+    }
+    const U z1 = shfl_x(v[0], 0);
+    U nxt = shfl_down_x(v[0], 1);
+    if (lane == 31) nxt = gx;
+    zor = 0;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const U hi = (k < 31) ? v[k + 1] : nxt;
+        v[k] = zigzag((U)(hi - v[k]));          // v now holds Z of columns 32*lane + k
+        zor |= v[k];
+    }
+    if (32u * lane + 32u >= m) {                 // pad columns (R11): only the last lanes
+        zor = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            if (32u * lane + k + 1u >= m) v[k] = 0;
+            zor |= v[k];
+        }
+    }
+    return z1;
+}
+
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
+    return (uint32_t)__popc((((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u);
+}
+
+// Launch 1, one chunk: everything up to the record size (see the file comment).
+template <bool F64>
+__device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, uint8_t *scratch, int lane,
+                              int &hint) {
     using T = Traits<F64>;
     using U = typename T::U;
     constexpr U ABS = F64 ? (U)0x7FFFFFFFFFFFFFFFull : (U)0x7FFFFFFFu;
-
     const uint32_t B = job.block;
     const uint64_t first = c * (uint64_t)B;
     const uint32_t m = (uint32_t)((job.n - first) < B ? (job.n - first) : B);
-    const uint64_t data_start = 32ull + 4ull * job.nchunks;
 
     // ---- 1. values, specials, maximum ------------------------------------------------------
     U v[32];
@@ -277,44 +319,15 @@ __device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t 
     }
     hint = alpha;
 
-    // ---- 3. G (Eq. 4) and Z (Eq. 5) ------------------------------------------------------------
-    U gx;
-    if (alpha >= 0) {
-#pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] = case1_g(v[k], alpha);
-        gx = case1_g(vx, alpha);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] = zigzag(v[k]);
-        gx = zigzag(vx);
-    }
-    const U z1 = shfl_x(v[0], 0);
-    U nxt = shfl_down_x(v[0], 1);
-    if (lane == 31) nxt = gx;
-    U zor = 0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        const U hi = (k < 31) ? v[k + 1] : nxt;
-        v[k] = zigzag((U)(hi - v[k]));          // v now holds Z of columns 32*lane + k
-        zor |= v[k];
-    }
-    if (32u * lane + 32u >= m) {                 // pad columns (R11): only the last lanes
-        zor = 0;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            if (32u * lane + k + 1u >= m) v[k] = 0;
-            zor |= v[k];
-        }
-    }
+    // ---- 3. G, Z, w ------------------------------------------------------------------------------
+    U zor;
+    (void)to_z<F64>(v, vx, alpha, m, lane, zor);
     zor = warp_or_x(zor);
     const int w = zor ? (T::W - (F64 ? __clzll((long long)zor) : __clz((int)zor))) : 0;
-    __syncwarp();                                // the staging buffer is reused below
 
-    // ---- 4. bit planes -> shared memory, non-zero bytes per row ---------------------------------
+    // ---- 4. non-zero bytes per row (bit planes in registers only) --------------------------------
     const uint32_t cols = chunk_cols(m);
-    const uint32_t nact = cols / 32u;            // lanes holding row bytes
     const uint32_t row_bytes = cols / 8u;
-    // lanes past the row (lane >= nact) hold only pad columns, i.e. zero plane words
     uint32_t packed[T::W / 4];
     {
         uint32_t a[32];
@@ -323,8 +336,7 @@ __device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t 
         transpose32(a);
 #pragma unroll
         for (int p = 0; p < 32; ++p) {
-            *reinterpret_cast<uint32_t *>(buf + kPlOff + (T::W - 1 - p) * 128 + 4 * lane) = a[p];
-            const uint32_t nzb = (uint32_t)__popc((((a[p] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | a[p]) & 0x80808080u);
+            const uint32_t nzb = nonzero_bytes(a[p]);
             if (p % 4 == 0) packed[p / 4] = nzb;
             else packed[p / 4] |= nzb << (8 * (p % 4));
         }
@@ -337,8 +349,7 @@ __device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t 
             transpose32(a);
 #pragma unroll
             for (int p = 0; p < 32; ++p) {
-                *reinterpret_cast<uint32_t *>(buf + kPlOff + (31 - p) * 128 + 4 * lane) = a[p];
-                const uint32_t nzb = (uint32_t)__popc((((a[p] & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | a[p]) & 0x80808080u);
+                const uint32_t nzb = nonzero_bytes(a[p]);
                 if (p % 4 == 0) packed[8 + p / 4] = nzb;
                 else packed[8 + p / 4] |= nzb << (8 * (p % 4));
             }
@@ -347,6 +358,7 @@ __device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t 
             for (int i = 8; i < 16; ++i) packed[i] = 0;
         }
     }
+    __syncwarp();
 #pragma unroll
     for (int i = 0; i < T::W / 4; ++i) {
         const uint32_t s = __reduce_add_sync(kFull, packed[i]);
@@ -354,7 +366,7 @@ __device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t 
     }
     __syncwarp();
 
-    // ---- 5. storage choice (Sec. 3.3), record size, offset (Sec. 3.4) --------------------------
+    // ---- 5. storage choice (Sec. 3.3) and record size ------------------------------------------
     uint32_t cost = 0;
     bool dense_lo = false, dense_hi = false;
     if (lane < w) {                              // plane `lane`
@@ -372,53 +384,67 @@ __device__ void compute_chunk(const Job &job, uint64_t t, uint8_t *buf, uint8_t 
     const uint32_t body = __reduce_add_sync(kFull, cost);
     const uint64_t dense_mask = (uint64_t)__ballot_sync(kFull, dense_lo) |
                                 ((uint64_t)__ballot_sync(kFull, dense_hi) << 32);
-    const uint32_t flag_bytes = ((uint32_t)w + 7u) / 8u;
-    const uint32_t hdr = 3u + T::Z1B + flag_bytes;
-    const uint32_t size = hdr + body;
-    publish_size(job.flags, c, size, lane);
-    pd.t = t;
-    pd.z1 = (uint64_t)z1;
-    pd.dense_mask = dense_mask;
-    pd.size = size;
-    pd.w = w;
-    pd.alpha_byte = alpha >= 0 ? alpha : T::A_SENT;
-    pd.beta_hat = beta_hat;
-    pd.valid = true;
-    (void)data_start;
+    const uint32_t size = 3u + T::Z1B + ((uint32_t)w + 7u) / 8u + body;
+    if (lane == 0) {
+        reinterpret_cast<uint32_t *>(job.out + 32)[c] = size;
+        job.flags[c] = pack_meta(alpha >= 0 ? alpha : T::A_SENT, beta_hat, w);
+        job.flags[job.nchunks + c] = dense_mask;
+    }
 }
 
-// Steps 5-6 of a computed chunk: offset (look-back), record assembly in place of its plane
-// words, and the copy to global memory.  Returns false when a bounded wait gave up.
+// Launch 3, one chunk: G, Z and the plane words again (alpha and w from the analysis), then
+// the record at its offset.  meta / dense: the chunk's workspace words; size: its record size.
 template <bool F64>
-__device__ bool finish_chunk(const Job &job, const Pend &pd, uint8_t *buf, int lane, Control *ctl) {
+__device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, unsigned long long meta,
+                           unsigned long long dense, uint32_t size) {
     using T = Traits<F64>;
-    const uint64_t c = pd.t - job.chunk_begin;
+    using U = typename T::U;
     const uint32_t B = job.block;
     const uint64_t first = c * (uint64_t)B;
     const uint32_t m = (uint32_t)((job.n - first) < B ? (job.n - first) : B);
     const uint64_t data_start = 32ull + 4ull * job.nchunks;
+    const uint32_t mb = (uint32_t)(meta >> kMetaShift);
+    const int alpha_byte = (int)(mb >> 12), beta_hat = (int)((mb >> 7) & 31u), w = (int)(mb & 127u);
+    const int alpha = alpha_byte == T::A_SENT ? -1 : alpha_byte;
+    const uint64_t rec_off = data_start + (meta & kOffMask);
+    if (rec_off + size > job.out_cap) return;    // the offsets launch reported the capacity error
+
+    // ---- G, Z and the plane words in shared memory --------------------------------------------
+    U v[32];
+    read_own<F64>(buf, lane, m, v);
+    U vx = 0;                                   // value 1024 of a 1025-value chunk
+    if (m > 1024u && lane == 31) vx = read_elem<F64>(buf, 1024);
+    __syncwarp();                                // the staging buffer is reused below
+    U zor;
+    const U z1 = to_z<F64>(v, vx, alpha, m, lane, zor);
+    {
+        uint32_t a[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) a[j] = (uint32_t)v[j ^ 7];
+        transpose32(a);
+#pragma unroll
+        for (int p = 0; p < 32; ++p)
+            *reinterpret_cast<uint32_t *>(buf + kPlOff + (T::W - 1 - p) * 128 + 4 * lane) = a[p];
+    }
+    if constexpr (F64) {
+        if (w > 32) {
+            uint32_t a[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) a[j] = (uint32_t)((uint64_t)v[j ^ 7] >> 32);
+            transpose32(a);
+#pragma unroll
+            for (int p = 0; p < 32; ++p) *reinterpret_cast<uint32_t *>(buf + kPlOff + (31 - p) * 128 + 4 * lane) = a[p];
+        }
+    }
+    __syncwarp();
+
     const uint32_t cols = chunk_cols(m);
     const uint32_t nact = cols / 32u;
     const uint32_t row_bytes = cols / 8u;
-    const int w = pd.w;
-    const uint32_t size = pd.size;
-    const uint64_t dense_mask = pd.dense_mask;
+    const uint64_t dense_mask = dense;
     const uint32_t flag_bytes = ((uint32_t)w + 7u) / 8u;
     const uint32_t hdr = 3u + T::Z1B + flag_bytes;
-
-    bool ok;
-    const uint64_t excl = lookback(job.flags, job.flags + job.nchunks, c, job.nchunks, size, lane, ctl, ok);
-    if (!ok) {
-        if (lane == 0) set_status(job.result, kErrTimeout);
-        return false;
-    }
-    const uint64_t rec_off = data_start + excl;
-    if (c + 1 == job.nchunks && lane == 0) job.result[0] = rec_off + size;
-    if (rec_off + size > job.out_cap) {          // also covers the header and size array
-        if (lane == 0) set_status(job.result, kErrCapacity);
-        return true;
-    }
-    if (lane == 0) *reinterpret_cast<uint32_t *>(job.out + 32 + 4 * c) = size;
+    struct { int alpha_byte, beta_hat; uint64_t z1; } pd{alpha_byte, beta_hat, (uint64_t)z1};
     uint8_t *gdst = job.out + rec_off;
     const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(gdst) & 15u);
 
@@ -475,20 +501,18 @@ __device__ bool finish_chunk(const Job &job, const Pend &pd, uint8_t *buf, int l
             for (uint32_t b = b0; b < b1; ++b) gbase[b] = buf[b];
         }
     }
-    if (c == 0 && lane == 0) {                   // the stream header, once per job
-        uint4 *dst = reinterpret_cast<uint4 *>(job.out);
-        dst[0] = make_uint4(0x4E434C46u, 1u | ((uint32_t)(F64 ? 0 : 1) << 8), B, 0u);
-        dst[1] = make_uint4((uint32_t)job.n, (uint32_t)(job.n >> 32), (uint32_t)job.nchunks,
-                            (uint32_t)(job.nchunks >> 32));
-    }
     __syncwarp();
-    return true;
+}
+
+__device__ __forceinline__ const Job &job_of(const Job *jobs, int njobs, const Job &single, uint64_t t) {
+    return (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
 }
 
 }  // namespace
 
+// Launch 1: analysis of every chunk (fixed stride per warp, next chunk prefetched).
 __global__ void __launch_bounds__(kThreads, 3)
-compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
+analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -497,78 +521,125 @@ compress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t to
     __shared__ Job s_single;                      // the single job, read from shared memory
     if (threadIdx.x == 0) s_single = single;
     __syncthreads();
-
-    // jobs without chunks (n = 0) still get a header and a length
-    {
-        const int gw = blockIdx.x * kWarpsPerCta + warp;
-        const int nw = gridDim.x * kWarpsPerCta;
-        const int nj = (jobs != nullptr) ? njobs : 1;
-        for (int j = gw; j < nj; j += nw) {
-            const Job &jb = (jobs != nullptr) ? jobs[j] : s_single;
-            if (jb.nchunks == 0 && lane == 0) {
-                uint4 *dst = reinterpret_cast<uint4 *>(jb.out);
-                if (jb.out_cap >= 32) {
-                    dst[0] = make_uint4(0x4E434C46u, 1u | (jb.dtype << 8), jb.block, 0u);
-                    dst[1] = make_uint4(0u, 0u, 0u, 0u);
-                    jb.result[0] = 32;
-                } else {
-                    set_status(jb.result, kErrCapacity);
-                }
-            }
-        }
-    }
-
-    // Two-stage pipeline per warp: chunk t is computed and its size published before the
-    // previous chunk's offset is resolved, so the look-back waits overlap useful work.
+    const uint64_t gw = (uint64_t)blockIdx.x * kWarpsPerCta + warp;
+    const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
+    if (gw >= total_chunks) return;
     int hint64 = -1, hint32 = -1;
     int cur = 0;
-    Pend pend;
-    pend.valid = false;
-    while (true) {
-        uint64_t t = 0;
-        if (lane == 0) t = atomicAdd(&ctl->ticket, 1ull);
-        t = shfl_u64(t, 0);
-        if (t >= total_chunks) break;
-        if (*reinterpret_cast<volatile unsigned int *>(&ctl->abort)) break;
-        const Job &job = (jobs == nullptr) ? s_single : jobs[find_job(jobs, njobs, t)];
-        uint8_t *buf = wbase + cur * kBuf;
-        issue_chunk(jobs, njobs, s_single, t, buf, lane);
+    issue_chunk(jobs, njobs, s_single, gw, wbase, lane);
+    cp_async_commit();
+    for (uint64_t t = gw; t < total_chunks; t += nw) {
+        const uint64_t tn = t + nw;
+        if (tn < total_chunks) issue_chunk(jobs, njobs, s_single, tn, wbase + (cur ^ 1) * kBuf, lane);
         cp_async_commit();
-        cp_async_wait_none();
+        cp_async_wait_prior();                   // the current chunk has landed
         __syncwarp();
-        Pend next;
-        if (job.dtype == 0) compute_chunk<true>(job, t, buf, scratch, lane, hint64, next);
-        else compute_chunk<false>(job, t, buf, scratch, lane, hint32, next);
-        if (pend.valid) {
-            const Job &pj = (jobs == nullptr) ? s_single : jobs[find_job(jobs, njobs, pend.t)];
-            const bool ok = (pj.dtype == 0) ? finish_chunk<true>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl)
-                                            : finish_chunk<false>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl);
-            if (!ok) return;
-        }
-        pend = next;
+        const Job &job = job_of(jobs, njobs, s_single, t);
+        const uint64_t c = t - job.chunk_begin;
+        if (job.dtype == 0) analyse_chunk<true>(job, c, wbase + cur * kBuf, scratch, lane, hint64);
+        else analyse_chunk<false>(job, c, wbase + cur * kBuf, scratch, lane, hint32);
+        __syncwarp();                            // this buffer is refilled next
         cur ^= 1;
     }
-    if (pend.valid) {
-        const Job &pj = (jobs == nullptr) ? s_single : jobs[find_job(jobs, njobs, pend.t)];
-        if (pj.dtype == 0) finish_chunk<true>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl);
-        else finish_chunk<false>(pj, pend, wbase + (cur ^ 1) * kBuf, lane, ctl);
+    cp_async_wait_none();
+}
+
+// Launch 2: chunk offsets (exclusive prefix of each job's size array, added to its workspace
+// words), the stream header, the stream length and the capacity check; one CTA per job.
+__global__ void __launch_bounds__(1024)
+compress_offsets_kernel(const Job *__restrict__ jobs, Job single) {
+    __shared__ uint64_t warp_sums[33];
+    const Job &job = (jobs == nullptr) ? single : jobs[blockIdx.x];
+    const uint64_t nc = job.nchunks;
+    const uint32_t *sizes = reinterpret_cast<const uint32_t *>(job.out + 32);
+    unsigned long long *meta = job.flags;
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < nc; base += 8192) {
+        const uint64_t i0 = base + 8ull * threadIdx.x;
+        uint32_t s[8];
+        if (i0 + 8 <= nc) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const uint4 x = *reinterpret_cast<const uint4 *>(sizes + i0 + 4 * q);
+                s[4 * q] = x.x; s[4 * q + 1] = x.y; s[4 * q + 2] = x.z; s[4 * q + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s[k] = (i0 + k < nc) ? sizes[i0 + k] : 0u;
+        }
+        uint64_t local = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) local += s[k];
+        uint64_t total;
+        uint64_t ex = carry + block_exclusive_scan(local, total, warp_sums);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (i0 + k < nc) meta[i0 + k] = (meta[i0 + k] & ~kOffMask) | ex;
+            ex += s[k];
+        }
+        carry += total;
     }
+    if (threadIdx.x == 0) {
+        const uint64_t bytes = 32ull + 4ull * nc + carry;
+        job.result[0] = bytes;
+        if (bytes > job.out_cap) set_status(job.result, kErrCapacity);
+        uint4 *dst = reinterpret_cast<uint4 *>(job.out);
+        dst[0] = make_uint4(0x4E434C46u, 1u | (job.dtype << 8), job.block, 0u);
+        dst[1] = make_uint4((uint32_t)job.n, (uint32_t)(job.n >> 32), (uint32_t)nc, (uint32_t)(nc >> 32));
+    }
+}
+
+// Launch 3: the records (fixed stride per warp, next chunk prefetched).
+__global__ void __launch_bounds__(kThreads, 3)
+emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    uint8_t *wbase = smem + warp * kWarpBytes;
+    __shared__ Job s_single;
+    if (threadIdx.x == 0) s_single = single;
+    __syncthreads();
+    const uint64_t gw = (uint64_t)blockIdx.x * kWarpsPerCta + warp;
+    const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
+    if (gw >= total_chunks) return;
+    int cur = 0;
+    issue_chunk(jobs, njobs, s_single, gw, wbase, lane);
+    cp_async_commit();
+    for (uint64_t t = gw; t < total_chunks; t += nw) {
+        const uint64_t tn = t + nw;
+        if (tn < total_chunks) issue_chunk(jobs, njobs, s_single, tn, wbase + (cur ^ 1) * kBuf, lane);
+        cp_async_commit();
+        const Job &job = job_of(jobs, njobs, s_single, t);
+        const uint64_t c = t - job.chunk_begin;
+        const unsigned long long meta = job.flags[c];
+        const unsigned long long dense = job.flags[job.nchunks + c];
+        const uint32_t size = reinterpret_cast<const uint32_t *>(job.out + 32)[c];
+        cp_async_wait_prior();                   // the current chunk has landed
+        __syncwarp();
+        if (job.dtype == 0) emit_chunk<true>(job, c, wbase + cur * kBuf, lane, meta, dense, size);
+        else emit_chunk<false>(job, c, wbase + cur * kBuf, lane, meta, dense, size);
+        __syncwarp();
+        cur ^= 1;
+    }
+    cp_async_wait_none();
 }
 
 constexpr int kCompressCtaSmem = kWarpsPerCta * kWarpBytes;
 
-static int g_occ_cache[64] = {0};
-static int g_sms_cache[64] = {0};
+namespace {
+int g_occ_cache[2][64] = {{0}};
+int g_sms_cache[64] = {0};
 
-int compress_grid(uint64_t total_chunks) {
+template <typename K>
+int persistent_grid(K kernel, int which, uint64_t total_chunks) {
     int dev = 0;
     cudaGetDevice(&dev);
-    int &occ_c = g_occ_cache[dev & 63];
+    int &occ_c = g_occ_cache[which][dev & 63];
     if (occ_c == 0) {
-        cudaFuncSetAttribute(compress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCompressCtaSmem);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCompressCtaSmem);
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, compress_kernel, kThreads, kCompressCtaSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, kCompressCtaSmem);
         g_sms_cache[dev & 63] = sms;
         occ_c = occ > 0 ? occ : 1;
     }
@@ -577,11 +648,22 @@ int compress_grid(uint64_t total_chunks) {
     const uint64_t need = (total_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
     return (int)(need < (uint64_t)cached ? (need > 0 ? need : 1) : (uint64_t)cached);
 }
+}  // namespace
+
+int compress_grid(uint64_t total_chunks) { return persistent_grid(emit_kernel, 1, total_chunks); }
 
 cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,
                             Control *ctl, cudaStream_t stream) {
-    const int grid = compress_grid(total_chunks);
-    compress_kernel<<<grid, kThreads, kCompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+    (void)ctl;
+    if (total_chunks > 0) {
+        const int g1 = persistent_grid(analyse_kernel, 0, total_chunks);
+        analyse_kernel<<<g1, kThreads, kCompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
+    }
+    compress_offsets_kernel<<<(d_jobs != nullptr) ? njobs : 1, 1024, 0, stream>>>(d_jobs, single);
+    if (total_chunks > 0) {
+        const int g3 = persistent_grid(emit_kernel, 1, total_chunks);
+        emit_kernel<<<g3, kThreads, kCompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
+    }
     return cudaGetLastError();
 }
 

@@ -286,25 +286,6 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     __syncwarp();
 }
 
-// block-wide exclusive scan of one u64 per thread (1024 threads); returns the block total
-__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t &total, uint64_t *warp_sums) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint64_t incl = v + warp_exclusive_u64(v, lane);
-    if (lane == 31) warp_sums[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const uint64_t ws = warp_sums[lane];
-        const uint64_t wincl = ws + warp_exclusive_u64(ws, lane);
-        warp_sums[lane] = wincl - ws;
-        if (lane == 31) warp_sums[32] = wincl;
-    }
-    __syncthreads();
-    const uint64_t r = warp_sums[warp] + incl - v;
-    total = warp_sums[32];
-    __syncthreads();
-    return r;
-}
-
 }  // namespace
 
 // Chunk offsets (exclusive prefix of the u32 size array) of every job into job.flags.

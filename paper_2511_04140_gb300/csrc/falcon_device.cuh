@@ -465,11 +465,28 @@ __device__ __forceinline__ uint64_t lookback(unsigned long long *f1, unsigned lo
     return excl;
 }
 
-// Look-back words a job needs: one per chunk and one per group of 32 chunks.
-__host__ __device__ __forceinline__ uint64_t lookback_words(uint64_t nchunks) { return nchunks + (nchunks + 31) / 32; }
 
 __device__ __forceinline__ void set_status(unsigned long long *result, uint32_t code) {
     atomicCAS(&result[1], 0ull, (unsigned long long)code);
+}
+
+// block-wide exclusive scan of one u64 per thread (1024 threads); returns the block total
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t &total, uint64_t *warp_sums) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t incl = v + warp_exclusive_u64(v, lane);
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint64_t ws = warp_sums[lane];
+        const uint64_t wincl = ws + warp_exclusive_u64(ws, lane);
+        warp_sums[lane] = wincl - ws;
+        if (lane == 31) warp_sums[32] = wincl;
+    }
+    __syncthreads();
+    const uint64_t r = warp_sums[warp] + incl - v;
+    total = warp_sums[32];
+    __syncthreads();
+    return r;
 }
 
 // Finds the job that owns global ticket t (jobs sorted by chunk_begin).

@@ -28,7 +28,7 @@ struct Job {
     uint64_t n;
     uint64_t nchunks;
     uint64_t chunk_begin;          // first global work ticket of this job
-    unsigned long long *flags;     // nchunks decoupled look-back words
+    unsigned long long *flags;     // the job's workspace words (workspace_words(nchunks))
     unsigned long long *result;    // [0] stream bytes (compress) / values (decompress), [1] status
     uint32_t block;
     uint32_t dtype;                // 0 = FP64, 1 = FP32
@@ -43,6 +43,10 @@ struct Control {
 static_assert(sizeof(Control) == 64, "control block is 64 bytes");
 
 constexpr size_t kControlBytes = 256;   // control block region (keeps flags 256-aligned)
+
+// Workspace words of a job: two per chunk (compression: the analysis results and offset,
+// and the dense-row mask; decompression: the chunk offsets in the first nchunks).
+__host__ __device__ constexpr uint64_t workspace_words(uint64_t nchunks) { return 2 * nchunks; }
 
 cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single,
                             uint64_t total_chunks, Control *ctl, cudaStream_t stream);

@@ -1,4 +1,4 @@
-// falcon_compress_noalloc: compression whose look-back scratch is a fixed device array of
+// falcon_compress_noalloc: compression whose workspace scratch is a fixed device array of
 // this file instead of caller- or library-allocated memory.  Host code plus one static
 // device symbol; the work itself is falcon_compress_async's.
 #include <mutex>
@@ -8,11 +8,11 @@
 
 namespace {
 
-// control block + one look-back word per chunk + one group word per 32 chunks, in the layout
-// falcon_workspace_bytes describes, for FALCON_NOALLOC_MAX_CHUNKS chunks
-constexpr size_t kWords = FALCON_NOALLOC_MAX_CHUNKS + (FALCON_NOALLOC_MAX_CHUNKS + 31) / 32;
+// control block + the per-chunk workspace words, in the layout falcon_workspace_bytes
+// describes, for FALCON_NOALLOC_MAX_CHUNKS chunks
+constexpr size_t kWords = falcon::workspace_words(FALCON_NOALLOC_MAX_CHUNKS);
 constexpr size_t kScratchBytes = falcon::kControlBytes + (8 * kWords + 255) / 256 * 256;
-static_assert(kScratchBytes == 540928, "scratch size as documented in falcon.h");
+static_assert(kScratchBytes == 1048832, "scratch size as documented in falcon.h");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 

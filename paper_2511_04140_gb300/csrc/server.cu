@@ -3,10 +3,10 @@
 // One worker thread per server repeats:
 //   1. take the newly submitted requests into the FIFO queue;
 //   2. admit from the head of the queue while the request's device block (input, output,
-//      look-back or offset words) fits the device arena and its output fits the host arena,
+//      per-chunk workspace words) fits the device arena and its output fits the host arena,
 //      at most max_batch requests and one batch slot per direction;
 //   3. per direction with admitted requests, enqueue
-//        up stream:      H2D inputs, zeroing of the look-back words            -> event U
+//        up stream:      H2D inputs                                           -> event U
 //        compute stream: wait U; job-table H2D; control/result reset; batched
 //                        persistent kernel; per-request result D2H             -> event K
 //        down stream:    (decompress only) wait K; output D2H into the host arena -> event O
@@ -98,7 +98,7 @@ struct Request {
     uint64_t in_bytes = 0, n = 0, nchunks = 0, out_cap = 0;
     int dtype = 0;
     uint32_t block = 0;
-    size_t words = 0;                  // look-back (compress) / chunk-offset (decompress) words
+    size_t words = 0;                  // per-chunk workspace words
     size_t dev_bytes = 0, dev_off = 0;
     size_t host_bytes = 0, host_off = 0;
     Clock::time_point t_submit;
@@ -267,8 +267,6 @@ struct falcon_server {
             total += r.nchunks;
             s.h_jobs[i] = j;
             if (r.in_bytes && cudaMemcpyAsync(d_in, r.h_in, r.in_bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
-                return FALCON_ERR_CUDA;
-            if (g.op == FALCON_COMPRESS && cudaMemsetAsync(words, 0, 8 * r.words, up) != cudaSuccess)
                 return FALCON_ERR_CUDA;
         }
         if (cudaEventRecord(s.up, up) != cudaSuccess) return FALCON_ERR_CUDA;
@@ -542,7 +540,7 @@ int falcon_server_submit(falcon_server *s, int op, const void *h_in, uint64_t co
     } else {
         return FALCON_ERR_INVALID;
     }
-    r.words = (size_t)(r.nchunks + (r.nchunks + 31) / 32);
+    r.words = (size_t)workspace_words(r.nchunks);
     r.dev_bytes = r.in_span() + r.out_span() + granules(8 * r.words);
     r.host_bytes = r.out_span();
     if (r.dev_bytes > s->st.device_capacity || r.host_bytes > s->st.host_capacity) return FALCON_ERR_CAPACITY;

@@ -2,7 +2,7 @@
 
 The scheduler is native (the library's worker thread, see include/falcon.h):
   - admission in arrival order against a device-memory budget: every request in flight
-    holds one block of a device arena of that size (input, output, look-back words), and
+    holds one block of a device arena of that size (input, output, workspace words), and
     its output one block of a page-locked host arena;
   - each pass of the worker turns everything admitted into ONE batched persistent launch per
     direction, with the uploads, the launch, the per-request result read-back (the paper's
