@@ -189,6 +189,26 @@ def release_caches(torch):
     getattr(torch._C, "_host_emptyCache", lambda: None)()
 
 
+def profiled_traffic(kernel: str):
+    """DRAM bytes per call of `kernel` from the committed ncu summary, or None when the
+    compression sources changed since the capture (the figure would no longer describe them)."""
+    import hashlib
+    import re
+    here = os.path.dirname(os.path.abspath(__file__))
+    try:
+        text = open(os.path.join(here, "profiles", "dram_traffic_segments_2e25.md")).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_call " + re.escape(kernel) + r" (\d+) sources ([0-9a-f]+)", text)
+    if not m:
+        return None
+    h = hashlib.sha256()
+    for f in ("compress.cu", "falcon_device.cuh", "falcon_internal.h", "falcon_tables.h"):
+        with open(os.path.join(here, "paper_2511_04140_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return int(m.group(1)) if h.hexdigest()[:16] == m.group(2) else None
+
+
 def max_over_ranks(x: float, dist, device) -> float:
     """The largest of every rank's x (the job ends when its slowest replica does)."""
     import torch
@@ -336,7 +356,7 @@ def main():
         "kernels": kstats,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": kstats[dom]["hbm_gbs"], "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": kstats[dom]["hbm_frac"],
-                     "traffic": None},
+                     "traffic": profiled_traffic(dom) if n == (1 << 26) else None},
         "clocks": clocks.summary(),
     }
     if rank == 0 and not args.no_e2e:
@@ -347,15 +367,14 @@ def main():
         torch.cuda.empty_cache()
         progress("batched launch")
         line["batched"] = bench_batched(falcon, synth, torch, dev, args.batch_series)
-    if rank == 0 and not args.no_serve:
-        release_caches(torch)
-        progress("server")
-        line["serve"] = bench_serve(args, dev)
-        release_caches(torch)
     if rank == 0 and not args.no_pipeline:
         release_caches(torch)
         progress("host pipeline")
         line["pipeline"] = bench_pipeline(falcon, synth, torch, dev, args.pipeline_values)
+        release_caches(torch)
+    if rank == 0 and not args.no_serve:
+        progress("server")
+        line["serve"] = bench_serve(args, dev)
         release_caches(torch)
     if rank == 0 and not args.no_cpu_baseline:
         progress("cpu baseline")
