@@ -178,11 +178,10 @@ __device__ __forceinline__ void issue_chunk(const Job *jobs, int njobs, const Jo
 }
 
 // Workspace words of a job (job.flags), written by the analysis launch:
-//   flags[c]            bits 47..63: alpha byte (5 bits) | beta_hat (5) | w (7); the offsets
-//                       launch adds the chunk's exclusive offset in bits 0..46;
-//   flags[nchunks + c]  the dense-row mask (bit p: plane p is stored dense).
+//   flags[c]            alpha byte (5 bits) | beta_hat (5) | w (7), in bits 47..63;
+//   flags[nchunks + c]  the dense-row mask (bit p: plane p is stored dense);
+// then, from the offsets launch, flags[2 nchunks + j] = the record offset of 64-chunk tile j.
 constexpr int kMetaShift = 47;
-constexpr unsigned long long kOffMask = (1ull << kMetaShift) - 1ull;
 
 __device__ __forceinline__ unsigned long long pack_meta(int alpha_byte, int beta_hat, int w) {
     return (unsigned long long)(((uint32_t)alpha_byte << 12) | ((uint32_t)beta_hat << 7) | (uint32_t)w) << kMetaShift;
@@ -393,10 +392,11 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
 }
 
 // Launch 3, one chunk: G, Z and the plane words again (alpha and w from the analysis), then
-// the record at its offset.  meta / dense: the chunk's workspace words; size: its record size.
+// the record at its offset.  meta / dense: the chunk's workspace words; size: its record size;
+// rel: its record offset relative to the first record.
 template <bool F64>
 __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, unsigned long long meta,
-                           unsigned long long dense, uint32_t size) {
+                           unsigned long long dense, uint32_t size, uint64_t rel) {
     using T = Traits<F64>;
     using U = typename T::U;
     const uint32_t B = job.block;
@@ -406,7 +406,7 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     const uint32_t mb = (uint32_t)(meta >> kMetaShift);
     const int alpha_byte = (int)(mb >> 12), beta_hat = (int)((mb >> 7) & 31u), w = (int)(mb & 127u);
     const int alpha = alpha_byte == T::A_SENT ? -1 : alpha_byte;
-    const uint64_t rec_off = data_start + (meta & kOffMask);
+    const uint64_t rec_off = data_start + rel;
     if (rec_off + size > job.out_cap) return;    // the offsets launch reported the capacity error
 
     // ---- G, Z and the plane words in shared memory --------------------------------------------
@@ -544,49 +544,37 @@ analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t tot
     cp_async_wait_none();
 }
 
-// Launch 2: chunk offsets (exclusive prefix of each job's size array, added to its workspace
-// words), the stream header, the stream length and the capacity check; one CTA per job.
+// Launch 2: record offsets per 64-chunk tile (exclusive prefix of each job's size array),
+// the stream header, the stream length and the capacity check; one CTA per job.
 __global__ void __launch_bounds__(1024)
 compress_offsets_kernel(const Job *__restrict__ jobs, Job single) {
     __shared__ uint64_t warp_sums[33];
     const Job &job = (jobs == nullptr) ? single : jobs[blockIdx.x];
     const uint64_t nc = job.nchunks;
-    const uint32_t *sizes = reinterpret_cast<const uint32_t *>(job.out + 32);
-    unsigned long long *meta = job.flags;
-    uint64_t carry = 0;
-    for (uint64_t base = 0; base < nc; base += 8192) {
-        const uint64_t i0 = base + 8ull * threadIdx.x;
-        uint32_t s[8];
-        if (i0 + 8 <= nc) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const uint4 x = *reinterpret_cast<const uint4 *>(sizes + i0 + 4 * q);
-                s[4 * q] = x.x; s[4 * q + 1] = x.y; s[4 * q + 2] = x.z; s[4 * q + 3] = x.w;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 8; ++k) s[k] = (i0 + k < nc) ? sizes[i0 + k] : 0u;
-        }
-        uint64_t local = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) local += s[k];
-        uint64_t total;
-        uint64_t ex = carry + block_exclusive_scan(local, total, warp_sums);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (i0 + k < nc) meta[i0 + k] = (meta[i0 + k] & ~kOffMask) | ex;
-            ex += s[k];
-        }
-        carry += total;
-    }
+    const uint64_t total = tile_prefix(reinterpret_cast<const uint32_t *>(job.out + 32), nc, job.flags + 2 * nc,
+                                       warp_sums);
     if (threadIdx.x == 0) {
-        const uint64_t bytes = 32ull + 4ull * nc + carry;
+        const uint64_t bytes = 32ull + 4ull * nc + total;
         job.result[0] = bytes;
         if (bytes > job.out_cap) set_status(job.result, kErrCapacity);
         uint4 *dst = reinterpret_cast<uint4 *>(job.out);
         dst[0] = make_uint4(0x4E434C46u, 1u | (job.dtype << 8), job.block, 0u);
         dst[1] = make_uint4((uint32_t)job.n, (uint32_t)(job.n >> 32), (uint32_t)nc, (uint32_t)(nc >> 32));
     }
+}
+
+// Per-chunk words of the emit launch, loaded one chunk ahead.
+struct EmitInfo {
+    unsigned long long meta, dense;
+    ChunkPos pos;
+};
+
+__device__ __forceinline__ EmitInfo load_info(const Job &job, uint64_t c, int lane) {
+    EmitInfo e;
+    e.meta = job.flags[c];
+    e.dense = job.flags[job.nchunks + c];
+    e.pos = load_pos(reinterpret_cast<const uint32_t *>(job.out + 32), job.flags + 2 * job.nchunks, c, lane);
+    return e;
 }
 
 // Launch 3: the records (fixed stride per warp, next chunk prefetched).
@@ -605,20 +593,29 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
     int cur = 0;
     issue_chunk(jobs, njobs, s_single, gw, wbase, lane);
     cp_async_commit();
+    EmitInfo info;
+    {
+        const Job &j0 = job_of(jobs, njobs, s_single, gw);
+        info = load_info(j0, gw - j0.chunk_begin, lane);
+    }
     for (uint64_t t = gw; t < total_chunks; t += nw) {
         const uint64_t tn = t + nw;
-        if (tn < total_chunks) issue_chunk(jobs, njobs, s_single, tn, wbase + (cur ^ 1) * kBuf, lane);
+        EmitInfo next{};
+        if (tn < total_chunks) {
+            issue_chunk(jobs, njobs, s_single, tn, wbase + (cur ^ 1) * kBuf, lane);
+            const Job &jn = job_of(jobs, njobs, s_single, tn);
+            next = load_info(jn, tn - jn.chunk_begin, lane);
+        }
         cp_async_commit();
         const Job &job = job_of(jobs, njobs, s_single, t);
         const uint64_t c = t - job.chunk_begin;
-        const unsigned long long meta = job.flags[c];
-        const unsigned long long dense = job.flags[job.nchunks + c];
-        const uint32_t size = reinterpret_cast<const uint32_t *>(job.out + 32)[c];
+        const uint64_t rel = resolve_pos(info.pos);
         cp_async_wait_prior();                   // the current chunk has landed
         __syncwarp();
-        if (job.dtype == 0) emit_chunk<true>(job, c, wbase + cur * kBuf, lane, meta, dense, size);
-        else emit_chunk<false>(job, c, wbase + cur * kBuf, lane, meta, dense, size);
+        if (job.dtype == 0) emit_chunk<true>(job, c, wbase + cur * kBuf, lane, info.meta, info.dense, info.pos.size, rel);
+        else emit_chunk<false>(job, c, wbase + cur * kBuf, lane, info.meta, info.dense, info.pos.size, rel);
         __syncwarp();
+        info = next;
         cur ^= 1;
     }
     cp_async_wait_none();

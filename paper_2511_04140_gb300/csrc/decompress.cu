@@ -43,21 +43,29 @@ __device__ __forceinline__ const Job &job_of(const Job *jobs, int njobs, const J
     return (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
 }
 
-// Offset (within the stream) and size of the record of ticket t, loaded early.
+// Offset (within the stream) and size of the record of ticket t: the loads are issued early
+// (locate), the offset is added up when the record is fetched (resolve).
 struct Loc {
     uint64_t t;
     uint64_t rec_off;
     uint32_t size;
+    ChunkPos pos;
 };
 
-__device__ __forceinline__ Loc locate(const Job *jobs, int njobs, const Job &single, uint64_t t) {
+__device__ __forceinline__ Loc locate(const Job *jobs, int njobs, const Job &single, uint64_t t, int lane) {
     const Job &job = job_of(jobs, njobs, single, t);
     const uint64_t c = t - job.chunk_begin;
     Loc l;
     l.t = t;
-    l.rec_off = 32ull + 4ull * job.nchunks + reinterpret_cast<const unsigned long long *>(job.flags)[c];
-    l.size = *reinterpret_cast<const uint32_t *>(job.in + 32 + 4 * c);
+    l.pos = load_pos(reinterpret_cast<const uint32_t *>(job.in + 32), job.flags, c, lane);
+    l.size = l.pos.size;
+    l.rec_off = 0;
     return l;
+}
+
+__device__ __forceinline__ void resolve(const Job *jobs, int njobs, const Job &single, Loc &l) {
+    const Job &job = job_of(jobs, njobs, single, l.t);
+    l.rec_off = 32ull + 4ull * job.nchunks + resolve_pos(l.pos);
 }
 
 __device__ __forceinline__ uint32_t max_record(uint32_t m, uint32_t dtype) {
@@ -288,35 +296,13 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
 
 }  // namespace
 
-// Chunk offsets (exclusive prefix of the u32 size array) of every job into job.flags.
+// Record offsets per 64-chunk tile (exclusive prefix of the u32 size array) of every job
+// into the first words of job.flags.
 __global__ void __launch_bounds__(1024)
 offsets_kernel(const Job *__restrict__ jobs, Job single) {
     __shared__ uint64_t warp_sums[33];
     const Job &job = (jobs == nullptr) ? single : jobs[blockIdx.x];
-    const uint64_t nc = job.nchunks;
-    const uint32_t *sizes = reinterpret_cast<const uint32_t *>(job.in + 32);
-    unsigned long long *off = job.flags;
-    uint64_t carry = 0;
-    for (uint64_t base = 0; base < nc; base += 4096) {
-        const uint64_t i0 = base + 4ull * threadIdx.x;
-        uint32_t s[4] = {0, 0, 0, 0};
-        if (i0 + 4 <= nc) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(sizes + i0);
-            s[0] = q.x; s[1] = q.y; s[2] = q.z; s[3] = q.w;
-        } else {
-            for (int k = 0; k < 4; ++k)
-                if (i0 + k < nc) s[k] = sizes[i0 + k];
-        }
-        const uint64_t local = (uint64_t)s[0] + s[1] + s[2] + s[3];
-        uint64_t total;
-        uint64_t ex = carry + block_exclusive_scan(local, total, warp_sums);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (i0 + k < nc) off[i0 + k] = ex;
-            ex += s[k];
-        }
-        carry += total;
-    }
+    (void)tile_prefix(reinterpret_cast<const uint32_t *>(job.in + 32), job.nchunks, job.flags, warp_sums);
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
@@ -338,18 +324,20 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
     }
     if (gw >= total_chunks) return;
     int cur = 0;
-    Loc lc = locate(jobs, njobs, s_single, gw);
+    Loc lc = locate(jobs, njobs, s_single, gw, lane);
+    resolve(jobs, njobs, s_single, lc);
     bool okc = issue_record(job_of(jobs, njobs, s_single, gw), lc, wbase, lane);
     cp_async_commit();
     Loc ln{};
-    if (gw + nw < total_chunks) ln = locate(jobs, njobs, s_single, gw + nw);
+    if (gw + nw < total_chunks) ln = locate(jobs, njobs, s_single, gw + nw, lane);
     for (uint64_t t = gw; t < total_chunks; t += nw) {
         const uint64_t tn = t + nw;
         bool okn = false;
         Loc lnn{};
         if (tn < total_chunks) {
+            resolve(jobs, njobs, s_single, ln);
             okn = issue_record(job_of(jobs, njobs, s_single, tn), ln, wbase + (cur ^ 1) * kBuf, lane);
-            if (tn + nw < total_chunks) lnn = locate(jobs, njobs, s_single, tn + nw);
+            if (tn + nw < total_chunks) lnn = locate(jobs, njobs, s_single, tn + nw, lane);
         }
         cp_async_commit();
         cp_async_wait_prior();                   // the current record has landed

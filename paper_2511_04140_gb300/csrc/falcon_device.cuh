@@ -489,6 +489,58 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t &t
     return r;
 }
 
+// Exclusive prefix of a stream's u32 size array per 64-chunk tile, into tile_off[0 ..
+// tile_count(nc)) (one 1024-thread block; 64 sizes per thread and step).  Returns the total
+// of all sizes (every thread).
+__device__ __forceinline__ uint64_t tile_prefix(const uint32_t *sizes, uint64_t nc, unsigned long long *tile_off,
+                                                uint64_t *warp_sums) {
+    const uint64_t ntiles = tile_count(nc);
+    uint64_t carry = 0;
+    for (uint64_t b = 0; b < ntiles; b += 1024) {
+        const uint64_t tile = b + threadIdx.x;
+        uint64_t sum = 0;
+        if (tile < ntiles) {
+            const uint64_t c0 = tile * kTile;
+            if (c0 + kTile <= nc) {
+                const uint4 *q = reinterpret_cast<const uint4 *>(sizes + c0);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const uint4 x = q[k];
+                    sum += (uint64_t)x.x + x.y + x.z + x.w;
+                }
+            } else {
+                for (uint64_t c = c0; c < nc; ++c) sum += sizes[c];
+            }
+        }
+        uint64_t total;
+        const uint64_t ex = carry + block_exclusive_scan(sum, total, warp_sums);
+        if (tile < ntiles) tile_off[tile] = ex;
+        carry += total;
+    }
+    return carry;
+}
+
+// Where chunk c's record starts (relative to the first record): its tile's offset plus the
+// sizes of the earlier chunks of the tile.  load_pos issues the loads (every lane), resolve_pos
+// adds them up (warp-collective) once they are needed, so their latency can be hidden.
+struct ChunkPos {
+    uint64_t tile;
+    uint32_t s0, s1, size;
+};
+__device__ __forceinline__ ChunkPos load_pos(const uint32_t *sizes, const unsigned long long *tile_off, uint64_t c,
+                                             int lane) {
+    const uint64_t t0 = c & ~(kTile - 1);
+    ChunkPos p;
+    p.tile = tile_off[c / kTile];
+    p.size = sizes[c];
+    p.s0 = (t0 + (uint64_t)lane < c) ? sizes[t0 + lane] : 0u;
+    p.s1 = (t0 + 32u + (uint64_t)lane < c) ? sizes[t0 + 32u + lane] : 0u;
+    return p;
+}
+__device__ __forceinline__ uint64_t resolve_pos(const ChunkPos &p) {
+    return p.tile + __reduce_add_sync(kFull, p.s0 + p.s1);       // a tile holds < 2^20 bytes
+}
+
 // Finds the job that owns global ticket t (jobs sorted by chunk_begin).
 __device__ __forceinline__ int find_job(const Job *jobs, int njobs, uint64_t t) {
     int lo = 0, hi = njobs - 1;

@@ -60,4 +60,4 @@ def test_stream_info_parses_oracle_streams(falcon_lib, oracle):
 def test_workspace_bytes(falcon_lib):
     assert falcon_lib.workspace_bytes(0) == 256
     assert falcon_lib.workspace_bytes(1) == 512
-    assert falcon_lib.workspace_bytes(65536) == 256 + 16 * 65536
+    assert falcon_lib.workspace_bytes(65536) == 256 + 8 * (2 * 65536 + 1024)
