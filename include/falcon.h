@@ -61,7 +61,7 @@ typedef enum {
     FALCON_ERR_CAPACITY = 2,    /* output buffer too small */
     FALCON_ERR_CORRUPT = 3,     /* malformed or truncated compressed stream */
     FALCON_ERR_CUDA = 4,        /* a CUDA runtime call failed */
-    FALCON_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (nothing hangs) */
+    FALCON_ERR_TIMEOUT = 5,     /* reserved: no kernel of this version waits on another warp */
     FALCON_ERR_UNSUPPORTED = 6  /* valid format parameter the GPU path does not handle */
 } falcon_status;
 

@@ -16,11 +16,6 @@
 namespace falcon {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr unsigned long long kFlagAgg = 1ull << 62;
-constexpr unsigned long long kFlagIncl = 2ull << 62;
-constexpr unsigned long long kValMask = (1ull << 62) - 1;
-// Bounded waits: a look-back spin gives up after this many SM clock cycles (~1.5 s).
-constexpr long long kSpinLimit = 3000000000ll;
 
 template <bool F64> struct Traits;
 template <> struct Traits<true> {
@@ -49,14 +44,6 @@ template <> struct Traits<false> {
 // --------------------------------------------------------------------------------------
 // small helpers
 // --------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -391,80 +378,6 @@ __device__ __forceinline__ uint32_t case1_g(uint32_t u, int a) {
     else N = (P + (1ull << (F - 1))) >> F;
     return (u >> 31) ? (0u - (uint32_t)N) : (uint32_t)N;
 }
-
-// --------------------------------------------------------------------------------------
-// Exclusive prefix of the chunk sizes of one job (Sec. 3.4), single pass, two levels.
-//
-// A one-level decoupled look-back resolves at most 32 chunks per L2 round trip, far fewer
-// than a GB300 finishes.  Here chunks are grouped by 32:
-//   f1[c]  chunk aggregate (its size), published as soon as the size is known;
-//   f2[q]  group q's aggregate (published by the group's last chunk once it has read the
-//          sizes of the chunks before it in the group) and later its inclusive prefix.
-// A chunk's exclusive prefix = sizes of the earlier chunks of its group (one 32-lane read)
-// + the exclusive prefix of its group (decoupled look-back over f2: 32 groups = 1024
-// chunks per round trip).  Every wait is on lower tickets only, and bounded: on timeout
-// (or when another warp already gave up) it sets ctl->abort and returns ok = false.
-// --------------------------------------------------------------------------------------
-__device__ __forceinline__ void publish_size(unsigned long long *f1, uint64_t c, uint64_t size, int lane) {
-    if (lane == 0) st_relaxed(&f1[c], kFlagAgg | size);
-}
-
-// Resolves the exclusive prefix of chunk c, whose size was already published.
-__device__ __forceinline__ uint64_t lookback(unsigned long long *f1, unsigned long long *f2, uint64_t c,
-                                             uint64_t nchunks, uint64_t size, int lane, Control *ctl,
-                                             bool &ok) {
-    ok = true;
-    const uint64_t q = c >> 5;
-    const uint32_t i = (uint32_t)(c & 31u);
-    const uint64_t gbeg = q << 5;
-    const bool last_in_group = (i == 31u) || (c + 1 == nchunks);
-    uint64_t within = 0, gpref = 0;
-    bool within_done = (i == 0), group_done = (q == 0), agg2_sent = false;
-    int64_t gtop = (int64_t)q - 1;
-    const long long t0 = clock64();
-    while (true) {
-        unsigned long long fa = kFlagAgg, fb = kFlagIncl;
-        if (!within_done && (uint32_t)lane < i) fa = ld_relaxed(&f1[gbeg + lane]);
-        if (!group_done) {
-            const int64_t gi = gtop - lane;
-            fb = (gi >= 0) ? ld_relaxed(&f2[gi]) : kFlagIncl;
-        }
-        if (!within_done && __all_sync(kFull, (fa >> 62) != 0ull)) {
-            within = warp_sum_u64(((uint32_t)lane < i) ? (fa & kValMask) : 0ull);
-            within_done = true;
-        }
-        if (within_done && last_in_group && !agg2_sent) {
-            if (lane == 0 && !group_done) st_relaxed(&f2[q], kFlagAgg | (within + size));
-            agg2_sent = true;
-        }
-        if (!group_done) {
-            const uint32_t st = (uint32_t)(fb >> 62);
-            const unsigned incl_mask = __ballot_sync(kFull, st == 2u);
-            const unsigned notready = __ballot_sync(kFull, st == 0u);
-            const int p = incl_mask ? __ffs(incl_mask) - 1 : 32;
-            const unsigned need = (p >= 31) ? kFull : ((2u << p) - 1u);
-            if (!(notready & need)) {
-                gpref += warp_sum_u64((lane <= p) ? (fb & kValMask) : 0ull);
-                if (p < 32) group_done = true;
-                else gtop -= 32;
-            }
-        }
-        if (within_done && group_done) break;
-        bool give_up = false;
-        if (lane == 0)
-            give_up = (clock64() - t0 > kSpinLimit) ||
-                      (*reinterpret_cast<volatile unsigned int *>(&ctl->abort) != 0);
-        if (__shfl_sync(kFull, give_up ? 1 : 0, 0)) {
-            if (lane == 0) atomicExch(&ctl->abort, 1u);
-            ok = false;
-            return 0;
-        }
-    }
-    const uint64_t excl = gpref + within;
-    if (last_in_group && lane == 0) st_relaxed(&f2[q], kFlagIncl | (excl + size));
-    return excl;
-}
-
 
 __device__ __forceinline__ void set_status(unsigned long long *result, uint32_t code) {
     atomicCAS(&result[1], 0ull, (unsigned long long)code);

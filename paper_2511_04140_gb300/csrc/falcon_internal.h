@@ -34,10 +34,11 @@ struct Job {
     uint32_t dtype;                // 0 = FP64, 1 = FP32
 };
 
-// Per-launch control block at the start of the workspace (zeroed before each launch).
+// Per-launch control block at the start of the workspace (zeroed before each launch); the
+// kernels of this version take their chunks in a fixed stride and do not use its fields.
 struct Control {
-    unsigned long long ticket;     // next work item
-    unsigned int abort;            // set when a bounded wait gives up; everyone bails out
+    unsigned long long ticket;     // reserved
+    unsigned int abort;            // reserved
     unsigned int pad[13];
 };
 static_assert(sizeof(Control) == 64, "control block is 64 bytes");

@@ -70,7 +70,6 @@ struct CachedSet {
     int n = 0;
     size_t in_bytes = 0, out_bytes = 0, ws_bytes = 0;
 };
-std::mutex g_cache_mu;
 CachedSet g_cache[64];
 
 int acquire_slots(int n, size_t in_bytes, size_t out_bytes, size_t ws_bytes, std::unique_lock<std::mutex> &hold,
