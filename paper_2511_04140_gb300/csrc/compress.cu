@@ -327,34 +327,29 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
     // ---- 4. non-zero bytes per row (bit planes in registers only) --------------------------------
     const uint32_t cols = chunk_cols(m);
     const uint32_t row_bytes = cols / 8u;
+    // one transpose body for both halves of an FP64 value (the high half only when w > 32):
+    // half h gives the counts of planes 32 h .. 32 h + 31
     uint32_t packed[T::W / 4];
-    {
+#pragma unroll
+    for (int i = 0; i < T::W / 4; ++i) packed[i] = 0;
+#pragma unroll 1
+    for (int h = 0; h < (F64 ? 2 : 1); ++h) {
+        if (h == 1 && w <= 32) break;
         uint32_t a[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) a[j] = (uint32_t)v[j ^ 7];
+        for (int j = 0; j < 32; ++j) a[j] = (uint32_t)((uint64_t)v[j ^ 7] >> (32 * h));
         transpose32(a);
+        uint32_t q[8];
 #pragma unroll
-        for (int p = 0; p < 32; ++p) {
-            const uint32_t nzb = nonzero_bytes(a[p]);
-            if (p % 4 == 0) packed[p / 4] = nzb;
-            else packed[p / 4] |= nzb << (8 * (p % 4));
-        }
-    }
-    if constexpr (F64) {
-        if (w > 32) {
-            uint32_t a[32];
+        for (int i = 0; i < 8; ++i) q[i] = 0;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) a[j] = (uint32_t)((uint64_t)v[j ^ 7] >> 32);
-            transpose32(a);
+        for (int p = 0; p < 32; ++p) q[p / 4] |= nonzero_bytes(a[p]) << (8 * (p % 4));
+        if (h == 0) {
 #pragma unroll
-            for (int p = 0; p < 32; ++p) {
-                const uint32_t nzb = nonzero_bytes(a[p]);
-                if (p % 4 == 0) packed[8 + p / 4] = nzb;
-                else packed[8 + p / 4] |= nzb << (8 * (p % 4));
-            }
-        } else {
+            for (int i = 0; i < 8; ++i) packed[i] = q[i];
+        } else if constexpr (F64) {
 #pragma unroll
-            for (int i = 8; i < 16; ++i) packed[i] = 0;
+            for (int i = 0; i < 8; ++i) packed[8 + i] = q[i];
         }
     }
     __syncwarp();
@@ -417,24 +412,18 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     __syncwarp();                                // the staging buffer is reused below
     U zor;
     const U z1 = to_z<F64>(v, vx, alpha, m, lane, zor);
-    {
+    // one transpose body for both halves of an FP64 value (the high half only when w > 32):
+    // half h holds planes 32 h .. 32 h + 31
+#pragma unroll 1
+    for (int h = 0; h < (F64 ? 2 : 1); ++h) {
+        if (h == 1 && w <= 32) break;
         uint32_t a[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) a[j] = (uint32_t)v[j ^ 7];
+        for (int j = 0; j < 32; ++j) a[j] = (uint32_t)((uint64_t)v[j ^ 7] >> (32 * h));
         transpose32(a);
+        uint8_t *dst = buf + kPlOff + (T::W - 1 - 32 * h) * 128 + 4 * lane;
 #pragma unroll
-        for (int p = 0; p < 32; ++p)
-            *reinterpret_cast<uint32_t *>(buf + kPlOff + (T::W - 1 - p) * 128 + 4 * lane) = a[p];
-    }
-    if constexpr (F64) {
-        if (w > 32) {
-            uint32_t a[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) a[j] = (uint32_t)((uint64_t)v[j ^ 7] >> 32);
-            transpose32(a);
-#pragma unroll
-            for (int p = 0; p < 32; ++p) *reinterpret_cast<uint32_t *>(buf + kPlOff + (31 - p) * 128 + 4 * lane) = a[p];
-        }
+        for (int p = 0; p < 32; ++p) *reinterpret_cast<uint32_t *>(dst - p * 128) = a[p];
     }
     __syncwarp();
 
