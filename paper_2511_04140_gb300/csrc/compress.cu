@@ -477,17 +477,22 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     }
     __syncwarp();
 
+    // to global memory: the 16-byte units entirely inside the record with one bulk copy
+    // (lane 0), the partial units at its ends (shared with the neighbouring records) bytewise
     uint8_t *gbase = gdst - sh;
     const uint32_t total = sh + size;
-    const uint32_t units = (total + 15u) / 16u;
-    for (uint32_t u = lane; u < units; u += 32) {
-        const uint32_t lo = 16u * u, hi = lo + 16u;
-        if (lo >= sh && hi <= total) {
-            *reinterpret_cast<uint4 *>(gbase + lo) = *reinterpret_cast<const uint4 *>(buf + lo);
-        } else {
-            const uint32_t b0 = lo > sh ? lo : sh;
-            const uint32_t b1 = hi < total ? hi : total;
-            for (uint32_t b = b0; b < b1; ++b) gbase[b] = buf[b];
+    const uint32_t u0 = (sh + 15u) / 16u, u1 = total / 16u;
+    if (u0 >= u1) {
+        for (uint32_t b = sh + (uint32_t)lane; b < total; b += 32) gbase[b] = buf[b];
+    } else {
+        const uint32_t head = 16u * u0 - sh, tail = total - 16u * u1;
+        if ((uint32_t)lane < head) gbase[sh + lane] = buf[sh + lane];
+        if ((uint32_t)lane < tail) gbase[16u * u1 + lane] = buf[16u * u1 + lane];
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+            bulk_store(gbase + 16u * u0, buf + 16u * u0, 16u * (u1 - u0));
+            bulk_commit();
         }
     }
     __syncwarp();
@@ -590,6 +595,8 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
     for (uint64_t t = gw; t < total_chunks; t += nw) {
         const uint64_t tn = t + nw;
         EmitInfo next{};
+        if (lane == 0) bulk_wait_read();         // the other buffer's record has left for global memory
+        __syncwarp();
         if (tn < total_chunks) {
             issue_chunk(jobs, njobs, s_single, tn, wbase + (cur ^ 1) * kBuf, lane);
             const Job &jn = job_of(jobs, njobs, s_single, tn);
@@ -608,6 +615,7 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
         cur ^= 1;
     }
     cp_async_wait_none();
+    if (lane == 0) bulk_wait();
 }
 
 constexpr int kCompressCtaSmem = kWarpsPerCta * kWarpBytes;
