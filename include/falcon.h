@@ -139,8 +139,9 @@ int falcon_release(void);
 
 /* ---------------------------------------------------------------------------------------
  * Batched form: many independent series (mixed lengths, dtypes and block sizes) compressed
- * or decompressed by ONE persistent kernel launch over all (series, chunk) work items
- * (decompression adds one small offsets launch).  Each series still produces / consumes
+ * or decompressed by the same launches as one series, each covering all (series, chunk) work
+ * items at once (compression: analysis, offsets, emit; decompression: offsets, decode).  Each
+ * series still produces / consumes
  * its own self-describing stream.  The paper processes one batch per kernel call (Alg. 1,
  * Alg. 3); this entry point is how the library serves many series at once.
  * ------------------------------------------------------------------------------------- */

@@ -221,7 +221,8 @@ def set_launch_config(compress_ctas_per_sm: int = 0, decompress_ctas_per_sm: int
 
 
 class Batch:
-    """A planned batched launch over many series (one persistent kernel per launch).
+    """A planned batched launch over many series (the launches of one direction, each covering
+    every (series, chunk) work item).
 
     compress:   Batch(COMPRESS, inputs=[tensor...], block=1024)       -> outputs: uint8 streams
     decompress: Batch(DECOMPRESS, inputs=[(stream_tensor, nbytes, header_bytes), ...])

@@ -1,4 +1,4 @@
-"""Batched form (one persistent launch over many series): every series' stream must be the
+"""Batched form (the launches of one direction over many series at once): every series' stream must be the
 oracle's stream for that series, byte for byte, and decode bit-exactly; results are the
 same alone, in the batch, and replayed from a CUDA graph."""
 import numpy as np
