@@ -250,9 +250,11 @@ typedef struct {
 
 /* Creates a server on CUDA device `device`: allocates both arenas (cudaMalloc and
  * cudaHostAlloc of the budgets) and starts the worker.  compute_streams >= 1;
- * 1 <= max_batch <= 65536.  *out receives the handle. */
+ * 1 <= max_batch <= 65536.  A batch also closes once its inputs reach max_batch_bytes (0: no
+ * byte limit; a larger single request still forms a batch), so that the uploads of one batch
+ * overlap the kernels and downloads of the previous ones.  *out receives the handle. */
 int falcon_server_create(int device, size_t device_budget_bytes, size_t host_budget_bytes,
-                         int compute_streams, int max_batch, falcon_server **out);
+                         int compute_streams, int max_batch, size_t max_batch_bytes, falcon_server **out);
 
 /* Queues one request; thread-safe.
  *   op = FALCON_COMPRESS:   h_in = count values of dtype, chunks of block_size values;

@@ -4,7 +4,8 @@
 //   1. take the newly submitted requests into the FIFO queue;
 //   2. admit from the head of the queue while the request's device block (input, output,
 //      per-chunk workspace words) fits the device arena and its output fits the host arena,
-//      at most max_batch requests and one batch slot per direction;
+//      at most max_batch requests (and max_batch_bytes of input, so that batches pipeline)
+//      and one batch slot per direction;
 //   3. per direction with admitted requests, enqueue
 //        up stream:      H2D inputs                                           -> event U
 //        compute stream: wait U; job-table H2D; control/result reset; batched
@@ -133,6 +134,7 @@ size_t elem(int dtype) { return dtype == FALCON_F64 ? 8 : 4; }
 struct falcon_server {
     int device = 0;
     int max_batch = 0;
+    size_t max_batch_bytes = 0;        // 0: no limit
     uint8_t *d_base = nullptr;
     Arena dev;                         // worker thread only
     uint8_t *h_base = nullptr;
@@ -200,18 +202,21 @@ struct falcon_server {
         Batch b[2];
         b[0].op = FALCON_COMPRESS;
         b[1].op = FALCON_DECOMPRESS;
+        size_t in_bytes[2] = {0, 0};
         {
             std::lock_guard<std::mutex> hl(host_mu);
             while (!pending.empty()) {
                 Request &r = pending.front();
                 Batch &g = b[r.op];
                 if (g.reqs.size() >= (size_t)max_batch) break;
+                if (max_batch_bytes && !g.reqs.empty() && in_bytes[r.op] + r.in_bytes > max_batch_bytes) break;
                 if (!g.slot && !(g.slot = take_slot())) break;
                 if (!dev.alloc(r.dev_bytes, &r.dev_off)) break;
                 if (!host.alloc(r.host_bytes, &r.host_off)) {
                     dev.release(r.dev_off, r.dev_bytes);
                     break;
                 }
+                in_bytes[r.op] += r.in_bytes;
                 g.reqs.push_back(r);
                 pending.pop_front();
             }
@@ -449,7 +454,7 @@ struct falcon_server {
 extern "C" {
 
 int falcon_server_create(int device, size_t device_budget_bytes, size_t host_budget_bytes, int compute_streams,
-                         int max_batch, falcon_server **out) {
+                         int max_batch, size_t max_batch_bytes, falcon_server **out) {
     if (!out || compute_streams < 1 || compute_streams > 64 || max_batch < 1 || max_batch > 65536 ||
         device_budget_bytes < kGranule || host_budget_bytes < kGranule)
         return FALCON_ERR_INVALID;
@@ -460,6 +465,7 @@ int falcon_server_create(int device, size_t device_budget_bytes, size_t host_bud
     auto *s = new falcon_server();
     s->device = device;
     s->max_batch = max_batch;
+    s->max_batch_bytes = max_batch_bytes;
     int st = FALCON_OK;
     auto ok = [&](cudaError_t e) {
         if (e != cudaSuccess && st == FALCON_OK) st = FALCON_ERR_CUDA;

@@ -98,7 +98,7 @@ def _load():
             L.falcon_compress_noalloc.restype = ci
             L.falcon_compress_noalloc.argtypes = [vp, u64, ci, u32, vp, sz, vp, vp]
             L.falcon_server_create.restype = ci
-            L.falcon_server_create.argtypes = [ci, sz, sz, ci, ci, c.POINTER(vp)]
+            L.falcon_server_create.argtypes = [ci, sz, sz, ci, ci, sz, c.POINTER(vp)]
             L.falcon_server_submit.restype = ci
             L.falcon_server_submit.argtypes = [vp, ci, vp, u64, ci, u32, u64]
             L.falcon_server_poll.restype = ci

@@ -43,14 +43,15 @@ class Server:
     (the server keeps a reference).  Futures carry `.latency` (seconds)."""
 
     def __init__(self, budget_bytes: int = 64 << 30, host_budget_bytes: int = 16 << 30, device="cuda",
-                 block: int = 1024, compute_streams: int = 4, max_batch: int = 1024):
+                 block: int = 1024, compute_streams: int = 8, max_batch: int = 1024,
+                 max_batch_bytes: int = 256 << 20):
         self.device = torch.device(device)
         index = self.device.index if self.device.index is not None else torch.cuda.current_device()
         self.block = block
         self._L = falcon.lib()
         h = ctypes.c_void_p()
         falcon._check(self._L.falcon_server_create(index, budget_bytes, host_budget_bytes, compute_streams,
-                                                   max_batch, ctypes.byref(h)), "server_create")
+                                                   max_batch, max_batch_bytes, ctypes.byref(h)), "server_create")
         self._h = h.value
         self._lock = threading.Lock()
         self._futs: dict = {}
