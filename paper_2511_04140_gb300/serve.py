@@ -43,8 +43,8 @@ class Server:
     (the server keeps a reference).  Futures carry `.latency` (seconds)."""
 
     def __init__(self, budget_bytes: int = 64 << 30, host_budget_bytes: int = 16 << 30, device="cuda",
-                 block: int = 1024, compute_streams: int = 8, max_batch: int = 1024,
-                 max_batch_bytes: int = 256 << 20):
+                 block: int = 1024, compute_streams: int = 16, max_batch: int = 1024,
+                 max_batch_bytes: int = 64 << 20):
         self.device = torch.device(device)
         index = self.device.index if self.device.index is not None else torch.cuda.current_device()
         self.block = block
