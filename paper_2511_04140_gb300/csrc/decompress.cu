@@ -22,15 +22,8 @@ namespace falcon {
 namespace {
 
 constexpr int kBuf = 8256;                  // one record (<= 8211 bytes at a 0..15 phase)
-constexpr int kPlane = 8192 + 128;          // 64 plane rows of 128 bytes + 64 u16 row positions
+constexpr int kPlane = 8192 + 128;          // 64 plane slots of 128 bytes + 64 u16 sparse-byte totals
 constexpr int kWarpBytes = 2 * kBuf + kPlane;
-
-// unaligned little-endian 32-bit read at byte i of a 16-byte aligned shared buffer
-__device__ __forceinline__ uint32_t ld_u32_unaligned(const uint8_t *b, uint32_t i) {
-    const uint32_t s = i & 3u;
-    const uint32_t *w = reinterpret_cast<const uint32_t *>(b + (i - s));
-    return __funnelshift_r(w[0], w[1], 8u * s);
-}
 
 __device__ __forceinline__ double div_pow10(int64_t g, int a) {
     return __ddiv_rn(__ll2double_rn(g), __longlong_as_double((long long)FALCON_P10_F64[a - FALCON_P10_F64_LO]));
@@ -95,6 +88,30 @@ __device__ __forceinline__ bool issue_record(const Job &job, const Loc &l, uint8
     return true;
 }
 
+// Copies len bytes from any byte address of a shared buffer to a 16-byte aligned one in
+// another buffer: one 16-byte store per lane and unit, built from two aligned 16-byte loads
+// and funnel shifts, then the tail bytes singly.  The source buffer has 16 readable bytes past
+// the copied bytes.
+__device__ __forceinline__ void copy_to_planes(uint8_t *dst, const uint8_t *src, uint32_t len, int lane) {
+    const uintptr_t sa = reinterpret_cast<uintptr_t>(src);
+    const uint32_t off = (uint32_t)(sa & 15u), k0 = off >> 2, sb = (off & 3u) * 8u;
+    const uint4 *S = reinterpret_cast<const uint4 *>(sa - off);
+    const uint32_t units = len >> 4;
+    for (uint32_t u = (uint32_t)lane; u < units; u += 32) {
+        const uint4 a = S[u], b = S[u + 1];
+        uint4 o;
+        switch (k0) {
+            case 0: o = make_uint4(__funnelshift_r(a.x, a.y, sb), __funnelshift_r(a.y, a.z, sb), __funnelshift_r(a.z, a.w, sb), __funnelshift_r(a.w, b.x, sb)); break;
+            case 1: o = make_uint4(__funnelshift_r(a.y, a.z, sb), __funnelshift_r(a.z, a.w, sb), __funnelshift_r(a.w, b.x, sb), __funnelshift_r(b.x, b.y, sb)); break;
+            case 2: o = make_uint4(__funnelshift_r(a.z, a.w, sb), __funnelshift_r(a.w, b.x, sb), __funnelshift_r(b.x, b.y, sb), __funnelshift_r(b.y, b.z, sb)); break;
+            default: o = make_uint4(__funnelshift_r(a.w, b.x, sb), __funnelshift_r(b.x, b.y, sb), __funnelshift_r(b.y, b.z, sb), __funnelshift_r(b.z, b.w, sb)); break;
+        }
+        *reinterpret_cast<uint4 *>(dst + 16u * u) = o;
+    }
+    const uint32_t tail = len & 15u;
+    if ((uint32_t)lane < tail) dst[16u * units + lane] = src[16u * units + lane];
+}
+
 template <bool F64>
 __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const uint8_t *rbuf, uint8_t *pbuf,
                              int lane) {
@@ -137,7 +154,7 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     // Sparse rows only (top to bottom): a sparse row's position is the header, the dense rows
     // above it (row_bytes each) and the sparse rows above it.  Dense rows need no walk.
     uint64_t sparse = bad ? 0ull : (~dense_mask & wmask);
-    uint32_t sparse_sum = 0, deficit = 0;
+    uint32_t sparse_sum = 0;
 #pragma unroll 1
     while (sparse && !bad) {
         const int p = 63 - __clzll((long long)sparse);
@@ -162,41 +179,47 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
 #pragma unroll
         for (int i = 0; i < 4; ++i)
             if ((nib >> (3 - i)) & 1u) x |= (uint32_t)rec[q++] << (8 * i);
-        *reinterpret_cast<uint32_t *>(pbuf + p * 128 + 4 * lane) = x;
+        *reinterpret_cast<uint32_t *>(pbuf + (63 - p) * 128 + 4 * lane) = x;
         sparse_sum += bm_bytes + nnz;
-        if (lane == 0) rowpos[p] = (uint16_t)(row_bytes - (bm_bytes + nnz));   // bytes saved
-        deficit += row_bytes - (bm_bytes + nnz);
+        if (lane == 0) rowpos[p] = (uint16_t)sparse_sum;   // sparse bytes through row p
     }
     if (!bad && hdr + row_bytes * (uint32_t)__popcll(dense_mask & wmask) + sparse_sum != size) bad = true;
     if (bad) {
         if (lane == 0) set_status(job.result, kErrCorrupt);
         return;
     }
-    (void)deficit;
     __syncwarp();
 
-    // ---- b. gather plane words, Z -> G -> values ------------------------------------------
-    // dense row p sits at hdr + row_bytes * (w-1-p) - (bytes saved by the sparse rows above p)
+    // ---- b. dense runs copied into the plane slots (plane p: slot 63 - p, 128 bytes, in
+    //      record order), then every plane word gathered with one aligned load ---------------
+    {
+        uint64_t dm = dense_mask & wmask;
+#pragma unroll 1
+        while (dm) {
+            const int p = 63 - __clzll((long long)dm);
+            const uint64_t below = (p >= 63) ? ~0ull : ((2ull << p) - 1ull);
+            const uint64_t holes = ~dense_mask & below;
+            const int q = (row_bytes == 128u) ? (holes ? 64 - __clzll((long long)holes) : 0) : p;
+            const uint64_t above = (p >= 63) ? 0ull : (wmask & ~((2ull << p) - 1ull));
+            const uint64_t sp_above = ~dense_mask & above;
+            // sparse bytes above p: the running total at the lowest sparse row above p
+            const uint32_t sbytes = sp_above ? (uint32_t)rowpos[__ffsll((long long)sp_above) - 1] : 0u;
+            const uint32_t rp = hdr + row_bytes * (uint32_t)__popcll(dense_mask & above) + sbytes;
+            copy_to_planes(pbuf + (63 - p) * 128, rec + rp, (uint32_t)(p - q + 1) * row_bytes, lane);
+            dm &= (q > 0) ? ((1ull << q) - 1ull) : 0ull;
+        }
+    }
+    __syncwarp();
+    auto plane_word = [&](int p) -> uint32_t {
+        const uint32_t x = *reinterpret_cast<const uint32_t *>(pbuf + (63 - p) * 128 + 4 * lane);
+        return ((uint32_t)p < w && active) ? x : 0u;
+    };
     U d[32];
-    uint32_t saved = 0;                          // running over p = w-1 .. 0
     if constexpr (F64) {
         if (w > 32) {
             uint32_t a[32];
 #pragma unroll
-            for (int i = 31; i >= 0; --i) {
-                const int p = i + 32;
-                uint32_t x = 0;
-                if ((uint32_t)p < w) {
-                    if ((dense_mask >> p) & 1ull) {
-                        const uint32_t rp = hdr + row_bytes * (w - 1u - (uint32_t)p) - saved;
-                        if (active) x = ld_u32_unaligned(rbuf, sh + rp + 4u * lane);
-                    } else {
-                        x = *reinterpret_cast<const uint32_t *>(pbuf + p * 128 + 4 * lane);
-                        saved += rowpos[p];
-                    }
-                }
-                a[i] = x;
-            }
+            for (int i = 0; i < 32; ++i) a[i] = plane_word(i + 32);
             transpose32(a);
 #pragma unroll
             for (int k = 0; k < 32; ++k) d[k] = (U)a[k ^ 7] << 32;
@@ -208,19 +231,7 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     {
         uint32_t a[32];
 #pragma unroll
-        for (int p = 31; p >= 0; --p) {
-            uint32_t x = 0;
-            if ((uint32_t)p < w) {
-                if ((dense_mask >> p) & 1ull) {
-                    const uint32_t rp = hdr + row_bytes * (w - 1u - (uint32_t)p) - saved;
-                    if (active) x = ld_u32_unaligned(rbuf, sh + rp + 4u * lane);
-                } else {
-                    x = *reinterpret_cast<const uint32_t *>(pbuf + p * 128 + 4 * lane);
-                    saved += rowpos[p];
-                }
-            }
-            a[p] = x;
-        }
+        for (int p = 0; p < 32; ++p) a[p] = plane_word(p);
         transpose32(a);
         if constexpr (F64) {
 #pragma unroll
