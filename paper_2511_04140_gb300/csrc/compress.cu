@@ -225,9 +225,9 @@ __device__ __forceinline__ typename Traits<F64>::U to_z(typename Traits<F64>::U 
     return z1;
 }
 
-__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
-    return (uint32_t)__popc((((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u);
-}
+// bit j of a nibble moved to bit 0 of byte j
+__device__ __forceinline__ uint32_t spread_nibble(uint32_t n) { return (n * 0x00204081u) & 0x01010101u; }
+
 
 // Launch 1, one chunk: everything up to the record size (see the file comment).
 template <bool F64>
@@ -293,22 +293,12 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
             const int e_max = floor_log10(vmax);
             const int atop = min(T::A_MAX, T::B_MAX - 1 - e_max);
             if (atop >= 0) {
-                // quick rejection: Alg. 2 on the largest magnitude first (one per lane)
-                U cand = 0;
-                bool has = (vx & ABS) == vmax;
-                if (has) cand = vx;
-#pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const bool is_max = (v[k] & ABS) == vmax;
-                    cand = is_max ? v[k] : cand;
-                    has |= is_max;
-                }
-                bool fail = false;
-                if (has) {
-                    if constexpr (F64) fail = !q_test(cand, atop);
-                    else fail = first_pass_f32(cand, atop) < 0;
-                }
-                if (!__any_sync(kFull, fail)) {
+                // quick rejection: Alg. 2 on the largest magnitude first.  The test reads
+                // only |v|, so it runs on vmax itself, the same in every lane.
+                bool fail;
+                if constexpr (F64) fail = !q_test(vmax, atop);
+                else fail = first_pass_f32(vmax, atop) < 0;
+                if (!fail) {
                     if constexpr (F64) alpha = search_alpha64(buf, lane, m, vx, atop, hint);
                     else alpha = alpha32(buf, lane, m, vx, atop);
                 }
@@ -324,32 +314,33 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
     zor = warp_or_x(zor);
     const int w = zor ? (T::W - (F64 ? __clzll((long long)zor) : __clz((int)zor))) : 0;
 
-    // ---- 4. non-zero bytes per row (bit planes in registers only) --------------------------------
+    // ---- 4. non-zero bytes per row, without forming the bit planes ----------------------------
+    // This lane's four bytes of row p cover its columns 8i .. 8i + 7 (i = 0..3); byte i is
+    // non-zero iff bit p is set in o[i], the OR of those columns' Z.  The four bits of every
+    // plane are added bit-sliced (count = b0 + 2 b1 + 4 b2) and spread into byte fields,
+    // planes 4g .. 4g + 3 in the bytes of packed[g].
     const uint32_t cols = chunk_cols(m);
     const uint32_t row_bytes = cols / 8u;
-    // one transpose body for both halves of an FP64 value (the high half only when w > 32):
-    // half h gives the counts of planes 32 h .. 32 h + 31
     uint32_t packed[T::W / 4];
+    {
+        U o[4];
 #pragma unroll
-    for (int i = 0; i < T::W / 4; ++i) packed[i] = 0;
-#pragma unroll 1
-    for (int h = 0; h < (F64 ? 2 : 1); ++h) {
-        if (h == 1 && w <= 32) break;
-        uint32_t a[32];
+        for (int i = 0; i < 4; ++i) {
+            U x = v[8 * i];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) a[j] = (uint32_t)((uint64_t)v[j ^ 7] >> (32 * h));
-        transpose32(a);
-        uint32_t q[8];
+            for (int j = 1; j < 8; ++j) x |= v[8 * i + j];
+            o[i] = x;
+        }
 #pragma unroll
-        for (int i = 0; i < 8; ++i) q[i] = 0;
+        for (int h = 0; h < T::W / 32; ++h) {
+            const uint32_t o0 = (uint32_t)((uint64_t)o[0] >> (32 * h)), o1 = (uint32_t)((uint64_t)o[1] >> (32 * h));
+            const uint32_t o2 = (uint32_t)((uint64_t)o[2] >> (32 * h)), o3 = (uint32_t)((uint64_t)o[3] >> (32 * h));
+            const uint32_t x1 = o0 ^ o1, x2 = o2 ^ o3, c1 = o0 & o1, c2 = o2 & o3;
+            const uint32_t b0 = x1 ^ x2, b1 = c1 ^ c2 ^ (x1 & x2), b2 = c1 & c2;
 #pragma unroll
-        for (int p = 0; p < 32; ++p) q[p / 4] |= nonzero_bytes(a[p]) << (8 * (p % 4));
-        if (h == 0) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) packed[i] = q[i];
-        } else if constexpr (F64) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) packed[8 + i] = q[i];
+            for (int g = 0; g < 8; ++g)
+                packed[8 * h + g] = spread_nibble((b0 >> (4 * g)) & 15u) | (spread_nibble((b1 >> (4 * g)) & 15u) << 1) |
+                                    (spread_nibble((b2 >> (4 * g)) & 15u) << 2);
         }
     }
     __syncwarp();
