@@ -308,10 +308,18 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
     }
     hint = alpha;
 
-    // ---- 3. G, Z, w ------------------------------------------------------------------------------
+    // ---- 3. G, Z, w (from the ORs of 8-column groups that step 4 uses) -------------------------
     U zor;
     (void)to_z<F64>(v, vx, alpha, m, lane, zor);
-    zor = warp_or_x(zor);
+    U o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        U x = v[8 * i];
+#pragma unroll
+        for (int j = 1; j < 8; ++j) x |= v[8 * i + j];
+        o[i] = x;
+    }
+    zor = warp_or_x((U)(o[0] | o[1] | o[2] | o[3]));
     const int w = zor ? (T::W - (F64 ? __clzll((long long)zor) : __clz((int)zor))) : 0;
 
     // ---- 4. non-zero bytes per row, without forming the bit planes ----------------------------
@@ -323,14 +331,6 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
     const uint32_t row_bytes = cols / 8u;
     uint32_t packed[T::W / 4];
     {
-        U o[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            U x = v[8 * i];
-#pragma unroll
-            for (int j = 1; j < 8; ++j) x |= v[8 * i + j];
-            o[i] = x;
-        }
 #pragma unroll
         for (int h = 0; h < T::W / 32; ++h) {
             const uint32_t o0 = (uint32_t)((uint64_t)o[0] >> (32 * h)), o1 = (uint32_t)((uint64_t)o[1] >> (32 * h));
@@ -403,9 +403,8 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     __syncwarp();                                // the staging buffer is reused below
     U zor;
     const U z1 = to_z<F64>(v, vx, alpha, m, lane, zor);
-    // one transpose body for both halves of an FP64 value (the high half only when w > 32):
-    // half h holds planes 32 h .. 32 h + 31
-#pragma unroll 1
+    // half h of the values holds planes 32 h .. 32 h + 31 (the high half only when w > 32)
+#pragma unroll
     for (int h = 0; h < (F64 ? 2 : 1); ++h) {
         if (h == 1 && w <= 32) break;
         uint32_t a[32];
