@@ -23,7 +23,7 @@ namespace {
 
 constexpr int kBuf = 8256;                  // one record (<= 8211 bytes at a 0..15 phase)
 constexpr int kPlane = 8192 + 128;          // 64 plane slots of 128 bytes + 64 u16 sparse-byte totals
-constexpr int kWarpBytes = 2 * kBuf + kPlane;
+constexpr int kWarpBytes = kBuf + kPlane;        // one record buffer, one plane buffer
 
 __device__ __forceinline__ double div_pow10(int64_t g, int a) {
     return __ddiv_rn(__ll2double_rn(g), __longlong_as_double((long long)FALCON_P10_F64[a - FALCON_P10_F64_LO]));
@@ -112,9 +112,11 @@ __device__ __forceinline__ void copy_to_planes(uint8_t *dst, const uint8_t *src,
     if ((uint32_t)lane < tail) dst[16u * units + lane] = src[16u * units + lane];
 }
 
-template <bool F64>
+// `next` starts the copy of the warp's next record into rbuf; it is called exactly once, as
+// soon as this record has been read completely.
+template <bool F64, class Next>
 __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const uint8_t *rbuf, uint8_t *pbuf,
-                             int lane) {
+                             int lane, Next &&next) {
     using T = Traits<F64>;
     using U = typename T::U;
 
@@ -186,6 +188,8 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     if (!bad && hdr + row_bytes * (uint32_t)__popcll(dense_mask & wmask) + sparse_sum != size) bad = true;
     if (bad) {
         if (lane == 0) set_status(job.result, kErrCorrupt);
+        __syncwarp();
+        next();
         return;
     }
     __syncwarp();
@@ -210,6 +214,7 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
         }
     }
     __syncwarp();
+    next();                                       // the record has been read
     auto plane_word = [&](int p) -> uint32_t {
         const uint32_t x = *reinterpret_cast<const uint32_t *>(pbuf + (63 - p) * 128 + 4 * lane);
         return ((uint32_t)p < w && active) ? x : 0u;
@@ -316,13 +321,13 @@ offsets_kernel(const Job *__restrict__ jobs, Job single) {
     (void)tile_prefix(reinterpret_cast<const uint32_t *>(job.in + 32), job.nchunks, job.flags, warp_sums);
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 3)
 decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     uint8_t *wbase = smem + warp * kWarpBytes;
-    uint8_t *pbuf = wbase + 2 * kBuf;
+    uint8_t *pbuf = wbase + kBuf;
     __shared__ Job s_single;                      // the single job, read from shared memory
     if (threadIdx.x == 0) s_single = single;
     __syncthreads();
@@ -334,7 +339,6 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
         if (lane == 0) jb.result[0] = jb.n;
     }
     if (gw >= total_chunks) return;
-    int cur = 0;
     Loc lc = locate(jobs, njobs, s_single, gw, lane);
     resolve(jobs, njobs, s_single, lc);
     bool okc = issue_record(job_of(jobs, njobs, s_single, gw), lc, wbase, lane);
@@ -345,21 +349,23 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
         const uint64_t tn = t + nw;
         bool okn = false;
         Loc lnn{};
-        if (tn < total_chunks) {
-            resolve(jobs, njobs, s_single, ln);
-            okn = issue_record(job_of(jobs, njobs, s_single, tn), ln, wbase + (cur ^ 1) * kBuf, lane);
-            if (tn + nw < total_chunks) lnn = locate(jobs, njobs, s_single, tn + nw, lane);
-        }
-        cp_async_commit();
-        cp_async_wait_prior();                   // the current record has landed
+        cp_async_wait_none();                    // the current record has landed
         __syncwarp();
+        // the next record goes into the same buffer once this one has been read
+        auto next = [&]() {
+            if (tn < total_chunks) {
+                resolve(jobs, njobs, s_single, ln);
+                okn = issue_record(job_of(jobs, njobs, s_single, tn), ln, wbase, lane);
+                if (tn + nw < total_chunks) lnn = locate(jobs, njobs, s_single, tn + nw, lane);
+            }
+            cp_async_commit();
+        };
         const Job &job = job_of(jobs, njobs, s_single, t);
-        if (job.dtype == 0) decode_chunk<true>(job, lc, okc, wbase + cur * kBuf, pbuf, lane);
-        else decode_chunk<false>(job, lc, okc, wbase + cur * kBuf, pbuf, lane);
+        if (job.dtype == 0) decode_chunk<true>(job, lc, okc, wbase, pbuf, lane, next);
+        else decode_chunk<false>(job, lc, okc, wbase, pbuf, lane, next);
         lc = ln;
         okc = okn;
         ln = lnn;
-        cur ^= 1;
     }
     cp_async_wait_none();
 }
