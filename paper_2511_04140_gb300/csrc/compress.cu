@@ -27,7 +27,8 @@ namespace {
 
 constexpr int kBuf = 8288;                  // one chunk of values / one record (+32 readable)
 constexpr int kScratch = 128;
-constexpr int kWarpBytes = 2 * kBuf + kScratch;
+constexpr int kWarpBytes = 2 * kBuf + kScratch;    // emit: two value / record buffers
+constexpr int kAnalyseWarpBytes = kBuf + kScratch;  // analysis: one value buffer
 constexpr int kPlOff = 48;                  // plane words: kPlOff + (W-1-p)*128 + 4*lane
 
 // Copies len bytes from src to dst inside a warp buffer, dst + 14 <= src (the move goes
@@ -229,10 +230,12 @@ __device__ __forceinline__ typename Traits<F64>::U to_z(typename Traits<F64>::U 
 __device__ __forceinline__ uint32_t spread_nibble(uint32_t n) { return (n * 0x00204081u) & 0x01010101u; }
 
 
-// Launch 1, one chunk: everything up to the record size (see the file comment).
-template <bool F64>
+// Launch 1, one chunk: everything up to the record size (see the file comment).  `next`
+// starts the copy of the warp's next chunk into buf; it is called once, as soon as the
+// staged values are no longer read (after the Case decision).
+template <bool F64, class Next>
 __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, uint8_t *scratch, int lane,
-                              int &hint) {
+                              int &hint, Next &&next) {
     using T = Traits<F64>;
     using U = typename T::U;
     constexpr U ABS = F64 ? (U)0x7FFFFFFFFFFFFFFFull : (U)0x7FFFFFFFu;
@@ -307,6 +310,8 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
         }
     }
     hint = alpha;
+    __syncwarp();
+    next();                                     // the staged values have been read
 
     // ---- 3. G, Z, w (from the ORs of 8-column groups that step 4 uses) -------------------------
     U zor;
@@ -494,14 +499,15 @@ __device__ __forceinline__ const Job &job_of(const Job *jobs, int njobs, const J
 
 }  // namespace
 
-// Launch 1: analysis of every chunk (fixed stride per warp, next chunk prefetched).
-__global__ void __launch_bounds__(kThreads, 3)
+// Launch 1: analysis of every chunk (fixed stride per warp; the next chunk is copied into
+// the warp's one value buffer while the current one is finished).
+__global__ void __launch_bounds__(kThreads, 4)
 analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint8_t *wbase = smem + warp * kWarpBytes;
-    uint8_t *scratch = wbase + 2 * kBuf;
+    uint8_t *wbase = smem + warp * kAnalyseWarpBytes;
+    uint8_t *scratch = wbase + kBuf;
     __shared__ Job s_single;                      // the single job, read from shared memory
     if (threadIdx.x == 0) s_single = single;
     __syncthreads();
@@ -509,21 +515,21 @@ analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t tot
     const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
     if (gw >= total_chunks) return;
     int hint64 = -1, hint32 = -1;
-    int cur = 0;
     issue_chunk(jobs, njobs, s_single, gw, wbase, lane);
     cp_async_commit();
     for (uint64_t t = gw; t < total_chunks; t += nw) {
         const uint64_t tn = t + nw;
-        if (tn < total_chunks) issue_chunk(jobs, njobs, s_single, tn, wbase + (cur ^ 1) * kBuf, lane);
-        cp_async_commit();
-        cp_async_wait_prior();                   // the current chunk has landed
+        cp_async_wait_none();                    // the current chunk has landed
         __syncwarp();
+        auto next = [&]() {
+            if (tn < total_chunks) issue_chunk(jobs, njobs, s_single, tn, wbase, lane);
+            cp_async_commit();
+        };
         const Job &job = job_of(jobs, njobs, s_single, t);
         const uint64_t c = t - job.chunk_begin;
-        if (job.dtype == 0) analyse_chunk<true>(job, c, wbase + cur * kBuf, scratch, lane, hint64);
-        else analyse_chunk<false>(job, c, wbase + cur * kBuf, scratch, lane, hint32);
-        __syncwarp();                            // this buffer is refilled next
-        cur ^= 1;
+        if (job.dtype == 0) analyse_chunk<true>(job, c, wbase, scratch, lane, hint64, next);
+        else analyse_chunk<false>(job, c, wbase, scratch, lane, hint32, next);
+        __syncwarp();
     }
     cp_async_wait_none();
 }
@@ -609,21 +615,22 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
 }
 
 constexpr int kCompressCtaSmem = kWarpsPerCta * kWarpBytes;
+constexpr int kAnalyseCtaSmem = kWarpsPerCta * kAnalyseWarpBytes;
 
 namespace {
 int g_occ_cache[2][64] = {{0}};
 int g_sms_cache[64] = {0};
 
 template <typename K>
-int persistent_grid(K kernel, int which, uint64_t total_chunks) {
+int persistent_grid(K kernel, int which, int smem_bytes, uint64_t total_chunks) {
     int dev = 0;
     cudaGetDevice(&dev);
     int &occ_c = g_occ_cache[which][dev & 63];
     if (occ_c == 0) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCompressCtaSmem);
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
         int sms = 0, occ = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, kCompressCtaSmem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem_bytes);
         g_sms_cache[dev & 63] = sms;
         occ_c = occ > 0 ? occ : 1;
     }
@@ -634,18 +641,18 @@ int persistent_grid(K kernel, int which, uint64_t total_chunks) {
 }
 }  // namespace
 
-int compress_grid(uint64_t total_chunks) { return persistent_grid(emit_kernel, 1, total_chunks); }
+int compress_grid(uint64_t total_chunks) { return persistent_grid(emit_kernel, 1, kCompressCtaSmem, total_chunks); }
 
 cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,
                             Control *ctl, cudaStream_t stream) {
     (void)ctl;
     if (total_chunks > 0) {
-        const int g1 = persistent_grid(analyse_kernel, 0, total_chunks);
-        analyse_kernel<<<g1, kThreads, kCompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
+        const int g1 = persistent_grid(analyse_kernel, 0, kAnalyseCtaSmem, total_chunks);
+        analyse_kernel<<<g1, kThreads, kAnalyseCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
     }
     compress_offsets_kernel<<<(d_jobs != nullptr) ? njobs : 1, 1024, 0, stream>>>(d_jobs, single);
     if (total_chunks > 0) {
-        const int g3 = persistent_grid(emit_kernel, 1, total_chunks);
+        const int g3 = persistent_grid(emit_kernel, 1, kCompressCtaSmem, total_chunks);
         emit_kernel<<<g3, kThreads, kCompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
     }
     return cudaGetLastError();
