@@ -27,7 +27,7 @@ namespace {
 
 constexpr int kBuf = 8288;                  // one chunk of values / one record (+32 readable)
 constexpr int kScratch = 128;
-constexpr int kWarpBytes = 2 * kBuf + kScratch;    // emit: two value / record buffers
+constexpr int kEmitWarpBytes = kBuf;               // emit: the plane / record buffer
 constexpr int kAnalyseWarpBytes = kBuf + kScratch;  // analysis: one value buffer
 constexpr int kPlOff = 48;                  // plane words: kPlOff + (W-1-p)*128 + 4*lane
 
@@ -382,6 +382,50 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
     }
 }
 
+// Lane reads its 32 values (indices 32 lane + k) from global memory, 16 bytes at a time when
+// the chunk is whole and 16-byte aligned; indices >= m read as +0.
+template <bool F64>
+__device__ __forceinline__ void load_own(const uint8_t *src, int lane, uint32_t m, typename Traits<F64>::U (&v)[32]) {
+    using U = typename Traits<F64>::U;
+    constexpr int UN = Traits<F64>::UNITS;
+    constexpr int PER = 32 / UN;
+    if (m >= 1024u && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        const uint4 *q4 = reinterpret_cast<const uint4 *>(src) + lane * UN;
+#pragma unroll
+        for (int u = 0; u < UN; ++u) {
+            const uint4 q = __ldg(q4 + u);
+            if constexpr (F64) {
+                v[PER * u + 0] = ((U)q.y << 32) | q.x;
+                v[PER * u + 1] = ((U)q.w << 32) | q.z;
+            } else {
+                v[PER * u + 0] = q.x;
+                v[PER * u + 1] = q.y;
+                v[PER * u + 2] = q.z;
+                v[PER * u + 3] = q.w;
+            }
+        }
+    } else {
+        const U *e = reinterpret_cast<const U *>(src);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t i = 32u * (uint32_t)lane + (uint32_t)k;
+            v[k] = i < m ? __ldg(e + i) : (U)0;
+        }
+    }
+}
+
+// Asks for chunk t's values to be brought into L2 (one prefetch per 128-byte line).
+__device__ __forceinline__ void prefetch_chunk(const Job *jobs, int njobs, const Job &single, uint64_t t, int lane) {
+    const Job &job = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
+    const uint64_t first = (t - job.chunk_begin) * (uint64_t)job.block;
+    const uint32_t m = (uint32_t)((job.n - first) < job.block ? (job.n - first) : job.block);
+    const uint32_t s = job.dtype == 0 ? 8u : 4u;
+    const uint8_t *src = job.in + first * s;
+    const uint8_t *end = src + (size_t)m * s;
+    for (const uint8_t *q = src + 128u * (uint32_t)lane; q < end; q += 128u * 32u)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
+}
+
 // Launch 3, one chunk: G, Z and the plane words again (alpha and w from the analysis), then
 // the record at its offset.  meta / dense: the chunk's workspace words; size: its record size;
 // rel: its record offset relative to the first record.
@@ -401,13 +445,15 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     if (rec_off + size > job.out_cap) return;    // the offsets launch reported the capacity error
 
     // ---- G, Z and the plane words in shared memory --------------------------------------------
+    const uint8_t *src = job.in + first * T::S;
     U v[32];
-    read_own<F64>(buf, lane, m, v);
+    load_own<F64>(src, lane, m, v);
     U vx = 0;                                   // value 1024 of a 1025-value chunk
-    if (m > 1024u && lane == 31) vx = read_elem<F64>(buf, 1024);
-    __syncwarp();                                // the staging buffer is reused below
+    if (m > 1024u && lane == 31) vx = __ldg(reinterpret_cast<const U *>(src) + 1024);
     U zor;
     const U z1 = to_z<F64>(v, vx, alpha, m, lane, zor);
+    if (lane == 0) bulk_wait_read();             // the previous record has left the buffer
+    __syncwarp();
     // half h of the values holds planes 32 h .. 32 h + 31 (the high half only when w > 32)
 #pragma unroll
     for (int h = 0; h < (F64 ? 2 : 1); ++h) {
@@ -567,22 +613,19 @@ __device__ __forceinline__ EmitInfo load_info(const Job &job, uint64_t c, int la
     return e;
 }
 
-// Launch 3: the records (fixed stride per warp, next chunk prefetched).
-__global__ void __launch_bounds__(kThreads, 3)
+// Launch 3: the records (fixed stride per warp; the next chunk's values are prefetched into L2).
+__global__ void __launch_bounds__(kThreads, 4)
 emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint8_t *wbase = smem + warp * kWarpBytes;
+    uint8_t *wbase = smem + warp * kEmitWarpBytes;
     __shared__ Job s_single;
     if (threadIdx.x == 0) s_single = single;
     __syncthreads();
     const uint64_t gw = (uint64_t)blockIdx.x * kWarpsPerCta + warp;
     const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
     if (gw >= total_chunks) return;
-    int cur = 0;
-    issue_chunk(jobs, njobs, s_single, gw, wbase, lane);
-    cp_async_commit();
     EmitInfo info;
     {
         const Job &j0 = job_of(jobs, njobs, s_single, gw);
@@ -591,30 +634,23 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
     for (uint64_t t = gw; t < total_chunks; t += nw) {
         const uint64_t tn = t + nw;
         EmitInfo next{};
-        if (lane == 0) bulk_wait_read();         // the other buffer's record has left for global memory
-        __syncwarp();
         if (tn < total_chunks) {
-            issue_chunk(jobs, njobs, s_single, tn, wbase + (cur ^ 1) * kBuf, lane);
+            prefetch_chunk(jobs, njobs, s_single, tn, lane);
             const Job &jn = job_of(jobs, njobs, s_single, tn);
             next = load_info(jn, tn - jn.chunk_begin, lane);
         }
-        cp_async_commit();
         const Job &job = job_of(jobs, njobs, s_single, t);
         const uint64_t c = t - job.chunk_begin;
         const uint64_t rel = resolve_pos(info.pos);
-        cp_async_wait_prior();                   // the current chunk has landed
-        __syncwarp();
-        if (job.dtype == 0) emit_chunk<true>(job, c, wbase + cur * kBuf, lane, info.meta, info.dense, info.pos.size, rel);
-        else emit_chunk<false>(job, c, wbase + cur * kBuf, lane, info.meta, info.dense, info.pos.size, rel);
+        if (job.dtype == 0) emit_chunk<true>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
+        else emit_chunk<false>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
         __syncwarp();
         info = next;
-        cur ^= 1;
     }
-    cp_async_wait_none();
     if (lane == 0) bulk_wait();
 }
 
-constexpr int kCompressCtaSmem = kWarpsPerCta * kWarpBytes;
+constexpr int kCompressCtaSmem = kWarpsPerCta * kEmitWarpBytes;
 constexpr int kAnalyseCtaSmem = kWarpsPerCta * kAnalyseWarpBytes;
 
 namespace {
