@@ -61,8 +61,94 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+class NvmlSampler:
+    """Samples the SM clock and the clock-event (throttle) reasons through NVML (the driver's
+    libnvidia-ml, loaded with ctypes) every few milliseconds while the timed region runs, so
+    that even a short region is covered.  Read-only queries."""
+
+    # nvmlClocksEventReasons bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, index: int, pci_bus: str | None = None, period_s: float = 0.002):
+        import ctypes
+        self.ct = ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.lib = lib
+        self.handle = ctypes.c_void_p()
+        # the CUDA device's own GPU (by PCI address), else NVML's device `index`
+        found = pci_bus is not None and lib.nvmlDeviceGetHandleByPciBusId_v2(
+            pci_bus.encode(), ctypes.byref(self.handle)) == 0
+        if not found and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.handle)) != 0:
+            raise RuntimeError("no NVML handle")
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(
+            self.handle, self.NVML_CLOCK_SM, ctypes.byref(mx)) == 0 else None
+        self.period = period_s
+        self.samples = []
+        self.recording = False
+        self.stop_flag = False
+        self.thread = None
+
+    def _one(self):
+        ct = self.ct
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.handle, self.NVML_CLOCK_SM, ct.byref(mhz)) != 0:
+            return None
+        if self.reasons_fn(self.handle, ct.byref(rs)) != 0:
+            return None
+        return float(mhz.value), int(rs.value)
+
+    def _run(self):
+        while not self.stop_flag:
+            if self.recording:
+                s = self._one()
+                if s is not None:
+                    self.samples.append(s)
+            time.sleep(self.period)
+
+    def start(self):
+        if self.thread is None:
+            self.thread = threading.Thread(target=self._run, daemon=True)
+            self.thread.start()
+
+    def __enter__(self):
+        self.start()
+        self.samples.clear()
+        first = self._one()                      # one sample at the start of the region
+        if first is not None:
+            self.samples.append(first)
+        self.recording = True
+        return self
+
+    def __exit__(self, *exc):
+        self.recording = False
+        last = self._one()                       # and one at its end
+        if last is not None:
+            self.samples.append(last)
+        self.stop_flag = True
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm = [m for m, _ in self.samples]
+        reasons = set()
+        for _, r in self.samples:
+            for bit, nm in self.REASONS.items():
+                if r & bit:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvml"}
+
+
 class ClockSampler:
-    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs
+    (used where NVML cannot be loaded)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -75,6 +161,7 @@ class ClockSampler:
 
     def __enter__(self):
         self.start()
+        self.lines.clear()
         return self
 
     def start(self):
@@ -122,7 +209,21 @@ class ClockSampler:
                 if val.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi"}
+
+
+def clock_sampler(index: int):
+    """NVML sampler if the driver's library loads, else the nvidia-smi one."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(index)
+        bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+    except Exception:
+        bus = None
+    try:
+        return NvmlSampler(index, bus)
+    except Exception:
+        return ClockSampler(index)
 
 
 # ------------------------------------------------------------------------------ reference arm
@@ -295,7 +396,7 @@ def main():
                 events[i][1].record(stream)
 
     progress("inputs resident; kernel steps")
-    clocks = ClockSampler(local)
+    clocks = clock_sampler(local)
     clocks.start()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -307,7 +408,6 @@ def main():
     ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in kernels]
           for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks.lines.clear()
     with clocks:
         torch.cuda.synchronize(dev)
         with torch.cuda.stream(stream):
