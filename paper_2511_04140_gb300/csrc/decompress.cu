@@ -32,6 +32,12 @@ __device__ __forceinline__ float div_pow10(int32_t g, int a) {
     return __fdiv_rn(__int2float_rn(g), __uint_as_float(FALCON_P10_F32[a - FALCON_P10_F32_LO]));
 }
 
+// number of set bits of a 4-bit value, with plain integer operations
+__device__ __forceinline__ uint32_t nibble_count(uint32_t n) {
+    const uint32_t x = n - ((n >> 1) & 5u);
+    return (x & 3u) + (x >> 2);
+}
+
 __device__ __forceinline__ const Job &job_of(const Job *jobs, int njobs, const Job &single, uint64_t t) {
     return (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
 }
@@ -156,20 +162,21 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     // Sparse rows only (top to bottom): a sparse row's position is the header, the dense rows
     // above it (row_bytes each) and the sparse rows above it.  Dense rows need no walk.
     uint64_t sparse = bad ? 0ull : (~dense_mask & wmask);
-    uint32_t sparse_sum = 0;
+    uint32_t sparse_sum = 0, walked = 0;       // sparse rows above the current one
 #pragma unroll 1
     while (sparse && !bad) {
         const int p = 63 - __clzll((long long)sparse);
         sparse &= ~(1ull << p);
-        const uint64_t above = (p >= 63) ? 0ull : (wmask & ~((2ull << p) - 1ull));
-        const uint32_t spos = hdr + row_bytes * (uint32_t)__popcll(dense_mask & above) + sparse_sum;
+        // rows above p: w - 1 - p, of which `walked` are sparse
+        const uint32_t spos = hdr + row_bytes * (w - 1u - (uint32_t)p - walked) + sparse_sum;
+        ++walked;
         if (spos + bm_bytes > size) { bad = true; break; }
         uint32_t nib = 0;
         if (active) {
             const uint32_t byte = rec[spos + (lane >> 1)];
             nib = (lane & 1) ? (byte & 0xFu) : (byte >> 4);
         }
-        const uint32_t cnt = __popc(nib);
+        const uint32_t cnt = nibble_count(nib);
         const unsigned b0 = __ballot_sync(kFull, cnt & 1u);
         const unsigned b1 = __ballot_sync(kFull, cnt & 2u);
         const unsigned b2 = __ballot_sync(kFull, cnt & 4u);
