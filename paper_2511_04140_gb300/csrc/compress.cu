@@ -90,7 +90,7 @@ __device__ __forceinline__ uint32_t sparse_row(uint8_t *buf, uint32_t P, uint32_
     const unsigned b2 = __ballot_sync(kFull, cnt & 4u);
     const unsigned lt = (1u << lane) - 1u;
     const uint32_t before = __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt);
-    const uint32_t total = __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2);
+    const uint32_t total = __reduce_add_sync(kFull, cnt);
     uint32_t q = P + nact / 2u + before;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {

@@ -182,7 +182,7 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
         const unsigned b2 = __ballot_sync(kFull, cnt & 4u);
         const unsigned lt = (1u << lane) - 1u;
         const uint32_t before = __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt);
-        const uint32_t nnz = __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2);
+        const uint32_t nnz = __reduce_add_sync(kFull, cnt);
         if (spos + bm_bytes + nnz > size) { bad = true; break; }
         uint32_t x = 0, q = spos + bm_bytes + before;
 #pragma unroll
