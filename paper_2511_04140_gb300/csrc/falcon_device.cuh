@@ -418,27 +418,49 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t &t
 }
 
 // Exclusive prefix of a stream's u32 size array per 64-chunk tile, into tile_off[0 ..
-// tile_count(nc)) (one 1024-thread block; 64 sizes per thread and step).  Returns the total
-// of all sizes (every thread).
+// tile_count(nc)) (one 1024-thread block, thread t owning tile t of each step of 1024 tiles).
+// Returns the total of all sizes (every thread).  A warp whose 32 tiles are all whole reads
+// their 8 KB of sizes coalesced (16-byte unit 32 k + lane, i.e. tiles 2k and 2k + 1 in the
+// two half-warps) and adds each tile up with half-warp shuffles in 32-bit arithmetic; a step
+// in which some 16-byte unit adds up to 2^26 or more (only in a malformed stream) falls back
+// to 64-bit sums per thread.
 __device__ __forceinline__ uint64_t tile_prefix(const uint32_t *sizes, uint64_t nc, unsigned long long *tile_off,
                                                 uint64_t *warp_sums) {
     const uint64_t ntiles = tile_count(nc);
+    const uint64_t full_tiles = nc / kTile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint64_t carry = 0;
     for (uint64_t b = 0; b < ntiles; b += 1024) {
         const uint64_t tile = b + threadIdx.x;
+        const uint64_t wt0 = b + 32u * (uint64_t)warp;
         uint64_t sum = 0;
-        if (tile < ntiles) {
-            const uint64_t c0 = tile * kTile;
-            if (c0 + kTile <= nc) {
-                const uint4 *q = reinterpret_cast<const uint4 *>(sizes + c0);
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const uint4 x = q[k];
-                    sum += (uint64_t)x.x + x.y + x.z + x.w;
-                }
-            } else {
-                for (uint64_t c = c0; c < nc; ++c) sum += sizes[c];
+        bool done = false;
+        if (wt0 + 32u <= full_tiles) {
+            const uint4 *q = reinterpret_cast<const uint4 *>(sizes + wt0 * kTile);
+            uint32_t mine = 0;
+            bool big = false;
+#pragma unroll 4
+            for (int k = 0; k < 16; ++k) {
+                const uint4 x = q[32 * k + lane];
+                const uint64_t s64 = (uint64_t)x.x + x.y + x.z + x.w;
+                big |= s64 >= (1ull << 26);
+                uint32_t s = (uint32_t)s64;
+                s += __shfl_xor_sync(kFull, s, 8);
+                s += __shfl_xor_sync(kFull, s, 4);
+                s += __shfl_xor_sync(kFull, s, 2);
+                s += __shfl_xor_sync(kFull, s, 1);
+                const uint32_t lo = __shfl_sync(kFull, s, 0), hi = __shfl_sync(kFull, s, 16);
+                if (lane == 2 * k) mine = lo;
+                if (lane == 2 * k + 1) mine = hi;
             }
+            done = !__any_sync(kFull, big);
+            sum = mine;
+        }
+        if (!done && tile < ntiles) {
+            sum = 0;
+            const uint64_t c0 = tile * kTile;
+            const uint64_t c1 = (c0 + kTile <= nc) ? c0 + kTile : nc;
+            for (uint64_t c = c0; c < c1; ++c) sum += sizes[c];
         }
         uint64_t total;
         const uint64_t ex = carry + block_exclusive_scan(sum, total, warp_sums);
