@@ -293,7 +293,6 @@ def release_caches(torch):
 def profiled_traffic(kernel: str):
     """DRAM bytes per call of `kernel` from the committed ncu summary, or None when the
     compression sources changed since the capture (the figure would no longer describe them)."""
-    import hashlib
     import re
     here = os.path.dirname(os.path.abspath(__file__))
     try:
@@ -303,11 +302,23 @@ def profiled_traffic(kernel: str):
     m = re.search(r"traffic_bytes_per_call " + re.escape(kernel) + r" (\d+) sources ([0-9a-f]+)", text)
     if not m:
         return None
+    return int(m.group(1)) if compress_sources_digest() == m.group(2) else None
+
+
+def compress_sources_digest() -> str:
+    """First 16 hex digits of sha256 over the compression kernels' sources with comments and
+    whitespace removed (a comment edit does not change the profiled kernels)."""
+    import hashlib
+    import re
+    here = os.path.dirname(os.path.abspath(__file__))
     h = hashlib.sha256()
     for f in ("compress.cu", "falcon_device.cuh", "falcon_internal.h", "falcon_tables.h"):
-        with open(os.path.join(here, "paper_2511_04140_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return int(m.group(1)) if h.hexdigest()[:16] == m.group(2) else None
+        with open(os.path.join(here, "paper_2511_04140_gb300", "csrc", f)) as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(" ".join(code.split()).encode())
+    return h.hexdigest()[:16]
 
 
 def max_over_ranks(x: float, dist, device) -> float:

@@ -1,21 +1,24 @@
 // Falcon compression (Sec. 3 of the paper; the work of Alg. 3 CmpKernel) for sm_103a, as
 // three launches, none of which waits on another warp:
-//   1. analyse: each warp takes chunks in a fixed stride (the next chunk's values already
-//      streaming into its second shared-memory buffer, cp.async, swizzled) and computes
+//   1. analyse: each warp takes chunks in a fixed stride (its one shared-memory value buffer
+//      receives the next chunk by cp.async, swizzled, as soon as the Case decision is done)
+//      and computes
 //      - the lane's 32 values, specials (R1) and the chunk maximum,
 //      - Case 1 / Case 2 of Eq. 4: the smallest decimal place alpha_max at which every value
 //        passes Alg. 2's test, in exact integer arithmetic (q_test); FP32 follows Alg. 2
 //        value by value,
 //      - G (Eq. 4), Z (Eq. 5) and the bit width w in registers,
-//      - 32x32 register transposes (one 32-bit word per bit plane: 4 row bytes per lane) and
-//        the non-zero bytes of every row (Sec. 3.3 lambda), sparse/dense per row, the record
-//        size, which goes into the stream's size array, and alpha, beta_hat, w and the
-//        dense-row mask, which go into the workspace;
+//      - the non-zero bytes of every row (Sec. 3.3 lambda) from ORs of 8-column groups,
+//        without forming the bit planes, sparse/dense per row, the record size, which goes
+//        into the stream's size array, and alpha, beta_hat, w and the dense-row mask, which
+//        go into the workspace;
 //   2. offsets: the exclusive prefix of each job's size array (the size synchronisation of
 //      Sec. 3.4), the stream header and length and the capacity check;
-//   3. emit: G, Z and the bit planes again from the kept alpha and w, the record assembled in
-//      shared memory at the output's 16-byte phase, in place of the plane words it consumes,
-//      and written with aligned 16-byte stores at its offset.
+//   3. emit: the values again (straight from global memory, the next chunk prefetched into
+//      L2), G, Z and the bit planes (32x32 register transposes, one 32-bit word per plane: 4
+//      row bytes per lane) from the kept alpha and w, the record assembled in shared memory at
+//      the output's 16-byte phase, in place of the plane words it consumes, and sent to its
+//      offset with one TMA bulk copy.
 // The paper resolves offsets inside one launch with a decoupled look-back; with about 1800
 // resident warps on a GB300 the waits of that look-back took half of every warp's time, while
 // the analysis recomputed by the emit launch costs less.

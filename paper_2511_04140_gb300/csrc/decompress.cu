@@ -3,15 +3,16 @@
 // 1. offsets_kernel: the chunk-size array is read and its exclusive prefix (the chunk
 //    offset array) is written to the workspace - the step Sec. 4 performs first.
 // 2. decompress_kernel: persistent; warp w decodes chunks w, w + W, w + 2W, ... (no
-//    ordering constraint remains).  Each warp starts the cp.async of its next record
-//    before decoding the current one; offsets are loaded one step earlier still.
-//    Decoding a record:
-//      a. header and flags; a walk over the rows that touches only sparse rows' bitmaps
-//         gives every row's position; sparse rows are expanded into the plane buffer,
-//      b. all plane words are gathered (dense rows straight from the record) into
-//         registers, two 32x32 transposes give Z, unzigzag + warp scan give G
-//         (inverse Eq. 5), Case 1 divides by 10^alpha (correctly rounded) and Case 2
-//         undoes the zigzag of the IEEE bits (inverse Eq. 4),
+//    ordering constraint remains).  Each warp has one record buffer: the cp.async of its
+//    next record starts as soon as the current one has been expanded into the plane buffer;
+//    offsets are loaded one step earlier still.  Decoding a record:
+//      a. header and flags; a walk over the sparse rows' bitmaps gives every row's
+//         position; sparse rows are expanded into their 128-byte plane slots,
+//      b. runs of dense rows are copied into their slots (16-byte funnel-shifted moves), all
+//         plane words are gathered into registers from fixed slot addresses, two 32x32
+//         transposes give Z, unzigzag + warp scan give G (inverse Eq. 5), Case 1 divides by
+//         10^alpha (correctly rounded) and Case 2 undoes the zigzag of the IEEE bits
+//         (inverse Eq. 4),
 //      c. values are staged (swizzled) and written with coalesced 16-byte stores.
 // Every read of a record is bounds-checked against its size; a malformed record sets
 // FALCON_ERR_CORRUPT and writes nothing.

@@ -219,3 +219,22 @@ def test_async_and_graph_capture(F, oracle):
         assert out[:nbytes].cpu().numpy().tobytes() == expect
         assert int(res2[1]) == 0 and int(res2[0]) == len(vals)
         assert np.array_equal(y.cpu().numpy().view(np.uint64), vals.view(np.uint64))
+
+
+def test_corrupt_size_in_a_long_stream(F, oracle):
+    """A stream long enough for whole 32-tile groups in the offsets scan (4096 chunks): a huge
+    size entry (only a malformed stream has one) must still be reported as corrupt."""
+    vals = synth.random_walk(1 << 22, seed=8)
+    good = bytearray(oracle.compress(vals, 1024))
+    for chunk in (5, 2100, 4095):
+        blob = bytearray(good)
+        blob[32 + 4 * chunk:36 + 4 * chunk] = (0xFFFFFFF0).to_bytes(4, "little")
+        st_o, _ = oracle.decompress_status(bytes(blob))
+        assert st_o == oracle.ERR_CORRUPT, chunk
+        s = torch.frombuffer(blob, dtype=torch.uint8).cuda()
+        with pytest.raises(F.FalconError) as e:
+            F.decompress(s)
+        assert e.value.status == F.ERR_CORRUPT, chunk
+    s = torch.frombuffer(good, dtype=torch.uint8).cuda()
+    y = F.decompress(s)
+    assert np.array_equal(_u(y.cpu().numpy()), _u(vals))
