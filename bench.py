@@ -507,7 +507,7 @@ def bench_batched(falcon, synth, torch, dev, count):
     orig = sum(x.numel() * x.element_size() for x in xs)
     nvals = sum(x.numel() for x in xs)
     sample = xs[::max(1, count // 128)]
-    tuned = tune.autotune(sample, blocks=(512, 1024, 1025), compress_ctas=(0, 2), decompress_ctas=(0, 1), reps=2)
+    tuned = tune.autotune(sample, blocks=(512, 1024, 1025), compress_ctas=(0, 3), decompress_ctas=(0, 2), reps=2)
     block = tune.apply(tuned["choice"])
     comp = falcon.Batch(falcon.COMPRESS, xs, block=block)
     stream = torch.cuda.current_stream(dev)

@@ -57,7 +57,7 @@ def measure(sample, block: int, c_ctas: int, d_ctas: int, reps: int = 3) -> dict
             "ratio": comp_bytes / orig}
 
 
-def autotune(sample, blocks=(512, 1024, 1025), compress_ctas=(0, 2), decompress_ctas=(0, 1),
+def autotune(sample, blocks=(512, 1024, 1025), compress_ctas=(0, 3), decompress_ctas=(0, 2),
              reps: int = 3, ratio_slack: float = 0.02) -> dict:
     """Returns the chosen configuration and the table of all candidates."""
     table = [measure(sample, b, c, d, reps) for b, c, d in itertools.product(blocks, compress_ctas, decompress_ctas)]
