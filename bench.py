@@ -305,12 +305,13 @@ def profiled_traffic(kernel: str):
     return int(m.group(1)) if compress_sources_digest() == m.group(2) else None
 
 
-def compress_sources_digest() -> str:
-    """First 16 hex digits of sha256 over the compression kernels' sources with comments and
-    whitespace removed (a comment edit does not change the profiled kernels)."""
+def compress_sources_digest(root: str | None = None) -> str:
+    """First 16 hex digits of sha256 over the compression kernels' sources (under `root`,
+    default this repository) with comments and whitespace removed: a comment edit does not
+    change the profiled kernels."""
     import hashlib
     import re
-    here = os.path.dirname(os.path.abspath(__file__))
+    here = root or os.path.dirname(os.path.abspath(__file__))
     h = hashlib.sha256()
     for f in ("compress.cu", "falcon_device.cuh", "falcon_internal.h", "falcon_tables.h"):
         with open(os.path.join(here, "paper_2511_04140_gb300", "csrc", f)) as fh:
