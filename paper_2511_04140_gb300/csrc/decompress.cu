@@ -24,7 +24,24 @@ namespace {
 
 constexpr int kBuf = 8256;                  // one record (<= 8211 bytes at a 0..15 phase)
 constexpr int kPlane = 8192 + 128;          // 64 plane slots of 128 bytes + 64 u16 sparse-byte totals
-constexpr int kWarpBytes = kBuf + kPlane;        // one record buffer, one plane buffer
+constexpr int kWarpBytes = kBuf + kPlane;
+
+// Byte-permute selector that spreads a lane's compacted non-zero bytes over its four row
+// bytes, by bitmap nibble n: row byte i (nibble bit 3 - i) takes the next compacted byte if
+// the bit is set, else a zero byte (selector 4, the zero operand).
+__shared__ uint32_t s_expand_sel[16];
+
+__device__ __forceinline__ void init_expand_sel() {
+    if (threadIdx.x < 16) {
+        const uint32_t n = threadIdx.x;
+        uint32_t sel = 0, r = 0;
+        for (int i = 0; i < 4; ++i) {
+            if ((n >> (3 - i)) & 1u) sel |= (r++) << (4 * i);
+            else sel |= 4u << (4 * i);
+        }
+        s_expand_sel[n] = sel;
+    }
+}        // one record buffer, one plane buffer
 
 __device__ __forceinline__ double div_pow10(int64_t g, int a) {
     return __ddiv_rn(__ll2double_rn(g), __longlong_as_double((long long)FALCON_P10_F64[a - FALCON_P10_F64_LO]));
@@ -185,10 +202,13 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
         const uint32_t before = __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt);
         const uint32_t nnz = __reduce_add_sync(kFull, cnt);
         if (spos + bm_bytes + nnz > size) { bad = true; break; }
-        uint32_t x = 0, q = spos + bm_bytes + before;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if ((nib >> (3 - i)) & 1u) x |= (uint32_t)rec[q++] << (8 * i);
+        // the lane's non-zero bytes start at record byte spos + bm_bytes + before: load the
+        // four bytes from there (two aligned words, at most 7 bytes past the record, inside
+        // the buffer) and put each in its place with one byte permute
+        const uint32_t qa = sh + spos + bm_bytes + before;
+        const uint32_t *wq = reinterpret_cast<const uint32_t *>(rbuf + (qa & ~3u));
+        const uint32_t word = __funnelshift_r(wq[0], wq[1], (qa & 3u) * 8u);
+        const uint32_t x = __byte_perm(word, 0u, s_expand_sel[nib]);
         *reinterpret_cast<uint32_t *>(pbuf + (63 - p) * 128 + 4 * lane) = x;
         sparse_sum += bm_bytes + nnz;
         if (lane == 0) rowpos[p] = (uint16_t)sparse_sum;   // sparse bytes through row p
@@ -338,6 +358,7 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
     uint8_t *pbuf = wbase + kBuf;
     __shared__ Job s_single;                      // the single job, read from shared memory
     if (threadIdx.x == 0) s_single = single;
+    init_expand_sel();
     __syncthreads();
     const uint64_t gw = (uint64_t)blockIdx.x * kWarpsPerCta + warp;
     const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
