@@ -238,3 +238,21 @@ def test_corrupt_size_in_a_long_stream(F, oracle):
     s = torch.frombuffer(good, dtype=torch.uint8).cuda()
     y = F.decompress(s)
     assert np.array_equal(_u(y.cpu().numpy()), _u(vals))
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_degenerate_series(F, oracle, dtype):
+    """Series whose chunks sit at the method's corners: all zeros and a constant (w = 0),
+    alternating signs (every row dense), consecutive integers (Case 1 at alpha = 0) and NaN
+    only (every chunk Case 2), each with a ragged tail."""
+    n = 5 * 1024 + 17
+    cases = {
+        "zeros": np.zeros(n, dtype=dtype),
+        "constant": np.full(n, 3.14, dtype=dtype),
+        "alternating": np.where(np.arange(n) % 2 == 0, 1.5, -1.5).astype(dtype),
+        "integers": np.arange(n).astype(dtype),
+        "nan": np.full(n, np.nan, dtype=dtype),
+    }
+    for name, vals in cases.items():
+        for block in (1024, 1025, 64):
+            check_parity(F, oracle, vals, block)
