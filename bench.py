@@ -496,6 +496,26 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    failed = failed_checks(line)
+    if failed:
+        sys.stderr.write("bench: bit-exactness check failed in " + ", ".join(failed) + "\n")
+        sys.exit(1)
+
+
+def failed_checks(obj, path="line"):
+    """Paths of every false `bit_exact` / `oracle_equal` key in the bench line: a lossless
+    codec that lost a bit, or a stream that differs from the oracle's, fails the run."""
+    bad = []
+    if isinstance(obj, dict):
+        for k, v in obj.items():
+            if k in ("bit_exact", "oracle_equal") and v is False:
+                bad.append(f"{path}.{k}")
+            else:
+                bad += failed_checks(v, f"{path}.{k}")
+    elif isinstance(obj, list):
+        for i, v in enumerate(obj):
+            bad += failed_checks(v, f"{path}[{i}]")
+    return bad
 
 
 def bench_batched(falcon, synth, torch, dev, count):

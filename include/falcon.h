@@ -35,9 +35,12 @@
  *     device; "h_" pointers are host pointers.  The caller owns every buffer it passes.
  *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
  *   - Value buffers must be aligned to the element size; stream buffers to 16 bytes.
- *   - Supported block sizes on the GPU: 2 <= block_size <= 1025 (the paper's n = 1025 and
- *     the 1024-value chunks are both in range).  Larger block sizes give
- *     FALCON_ERR_UNSUPPORTED.
+ *   - Block sizes: 2 <= block_size <= 1025 (FALCON_MAX_BLOCK).  Sec. 3.3 chooses chunks of
+ *     n = 64k + 1 values so that every row of the transposed bit-plane matrix is byte-aligned
+ *     and uses n = 1025 (k = 16); the format of this library takes k <= 16 (and any other
+ *     n up to 1025, with the zero-pad columns of a partial row).  Larger block sizes are
+ *     invalid everywhere: FALCON_ERR_INVALID from the compression entry points, 0 from
+ *     falcon_bound, FALCON_ERR_CORRUPT for a stream header that names one.
  */
 #ifndef FALCON_H_
 #define FALCON_H_
@@ -62,7 +65,7 @@ typedef enum {
     FALCON_ERR_CORRUPT = 3,     /* malformed or truncated compressed stream */
     FALCON_ERR_CUDA = 4,        /* a CUDA runtime call failed */
     FALCON_ERR_TIMEOUT = 5,     /* reserved: no kernel of this version waits on another warp */
-    FALCON_ERR_UNSUPPORTED = 6  /* valid format parameter the GPU path does not handle */
+    FALCON_ERR_UNSUPPORTED = 6  /* a request beyond a documented limit (FALCON_NOALLOC_MAX_CHUNKS) */
 } falcon_status;
 
 /* Library version (FALCON_ABI_VERSION). */
@@ -73,11 +76,18 @@ const char *falcon_status_string(int status);
 
 /* Worst-case stream size in bytes for n values of `dtype` in chunks of block_size:
  * 32 + 4*ceil(n/B) + sum over chunks of (2 + z1 + 1 + W/8 + W*cols/8), W = 64 (FP64) or 32,
- * z1 = W/8 bytes.  Pure host function; returns 0 for invalid arguments. */
+ * z1 = W/8 bytes.  The paper fixes only the chunk record (Sec. 3.3, Fig. 8: every row dense
+ * at w = W is its largest form) and "size array, then chunk data" (Sec. 3.4); the 32-byte
+ * header and the u32 size entries are this library's stream format.  Pure host function;
+ * returns 0 for invalid arguments (dtype, or block_size outside 2..1025). */
 size_t falcon_bound(uint64_t n, int dtype, uint32_t block_size);
 
-/* Parses the 32-byte header of a stream held in HOST memory (len >= 32).
- * Outputs may be NULL.  FALCON_ERR_CORRUPT if the header is malformed. */
+/* Parses the 32-byte header of a stream held in HOST memory (len >= 32).  The header is this
+ * library's own (the paper's batch output is the size array and the chunk data, Sec. 3.4,
+ * with no header): "FLCN", version 1, dtype, block_size, n and the number of chunks.
+ * Outputs may be NULL.  FALCON_ERR_INVALID for a NULL h_header; FALCON_ERR_CORRUPT if the
+ * header is malformed (magic, version, dtype, block_size outside 2..1025, or a chunk count
+ * other than ceil(n / block_size)). */
 int falcon_stream_info(const void *h_header, size_t len, uint64_t *n, int *dtype,
                        uint32_t *block_size, uint64_t *num_chunks);
 
@@ -128,13 +138,18 @@ int falcon_decompress_async(const void *d_in, size_t in_bytes, const void *h_hea
  *   - Every call on a device uses the same array: calls that overlap in time (two streams,
  *     or two host threads without ordering) race and corrupt each other's output; order
  *     them on one stream.
- *   - More than FALCON_NOALLOC_MAX_CHUNKS chunks: FALCON_ERR_UNSUPPORTED, nothing enqueued.
- * Arguments, d_result and the other errors are those of falcon_compress_async. */
+ *   - The looked-up address belongs to the device's current context: after a context reset
+ *     (cudaDeviceReset) call falcon_release() before the next call, which then looks the
+ *     address up again.
+ *   - Arguments are checked first, with the errors of falcon_compress_async; then more than
+ *     FALCON_NOALLOC_MAX_CHUNKS chunks gives FALCON_ERR_UNSUPPORTED, with nothing enqueued.
+ * d_result is as for falcon_compress_async. */
 #define FALCON_NOALLOC_MAX_CHUNKS 65536
 int falcon_compress_noalloc(const void *d_in, uint64_t n, int dtype, uint32_t block_size,
                             void *d_out, size_t out_capacity, uint64_t *d_result, void *stream);
 
-/* Frees the workspaces cached by falcon_compress / falcon_decompress on every device. */
+/* Frees the workspaces cached by falcon_compress / falcon_decompress and the host pipeline
+ * on every device, and forgets the scratch addresses of falcon_compress_noalloc. */
 int falcon_release(void);
 
 /* ---------------------------------------------------------------------------------------
@@ -262,7 +277,7 @@ int falcon_server_create(int device, size_t device_budget_bytes, size_t host_bud
  * h_in must stay valid and unchanged until the request's completion has been polled.
  * Returns FALCON_OK (exactly one completion with `tag` follows) or, with nothing queued:
  * FALCON_ERR_INVALID (arguments, or the server is shutting down), FALCON_ERR_CORRUPT (the
- * stream header is malformed), FALCON_ERR_UNSUPPORTED (block size), FALCON_ERR_CAPACITY (the
+ * stream header is malformed), FALCON_ERR_CAPACITY (the
  * request's device block or output can never fit the arenas), FALCON_ERR_CUDA (a CUDA call
  * of the server failed earlier; the server accepts no more work). */
 int falcon_server_submit(falcon_server *server, int op, const void *h_in, uint64_t count,

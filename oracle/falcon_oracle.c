@@ -41,6 +41,8 @@
  *   R13 the u32 size array precedes the records.
  *   R14 FP32: alpha <= 10, beta <= 7, mu = |x| * 2^-23, x = v * 10^alpha computed exactly
  *       (in FP64), round trip and decode are fl32((float)g / (float)10^alpha).
+ *   R16 block sizes: 2 <= B <= 1025 (Sec. 3.3's n = 64k + 1 with the implementation's
+ *       n = 1025 as the largest chunk).
  *
  * Stream layout (little-endian):
  *   0  "FLCN"  4  version=1 (u8)  5  dtype (u8: 0=f64, 1=f32)  6  reserved u16 = 0
@@ -60,7 +62,9 @@ enum { OR_F64 = 0, OR_F32 = 1 };
 enum { OR_OK = 0, OR_ERR_INVALID = 1, OR_ERR_CAPACITY = 2, OR_ERR_CORRUPT = 3 };
 
 #define OR_HEADER_BYTES 32u
-#define OR_MAX_BLOCK 65537u
+/* Sec. 3.3 makes chunks of n = 64k + 1 values (rows of the transposed matrix byte-aligned)
+   and the implementation uses n = 1025; the stream format takes n <= 1025 (k <= 16). */
+#define OR_MAX_BLOCK 1025u
 
 /* ------------------------------------------------------------------------------------ */
 /* Powers of ten, correctly rounded, from the C library's decimal parser.               */

@@ -11,6 +11,7 @@
 using namespace falcon;
 
 void falcon_pipeline_release();
+void falcon_noalloc_release();
 
 namespace falcon {
 int g_ctas_per_sm[2] = {0, 0};
@@ -24,8 +25,7 @@ uint64_t num_chunks(uint64_t n, uint32_t block) { return (n + block - 1) / block
 size_t elem_bytes(int dtype) { return dtype == FALCON_F64 ? 8 : 4; }
 
 int check_block(uint32_t block) {
-    if (block < 2 || block > 65537) return FALCON_ERR_INVALID;
-    if (block > kMaxBlock) return FALCON_ERR_UNSUPPORTED;
+    if (block < 2 || block > kMaxBlock) return FALCON_ERR_INVALID;
     return FALCON_OK;
 }
 
@@ -79,14 +79,17 @@ int parse_header(const uint8_t *h, size_t len, Header *out) {
     std::memcpy(&r.n, h + 16, 8);
     std::memcpy(&r.nchunks, h + 24, 8);
     if (r.dtype != FALCON_F64 && r.dtype != FALCON_F32) return FALCON_ERR_CORRUPT;
-    if (r.block < 2 || r.block > 65537) return FALCON_ERR_CORRUPT;
+    if (r.block < 2 || r.block > kMaxBlock) return FALCON_ERR_CORRUPT;
     if (r.nchunks != num_chunks(r.n, r.block)) return FALCON_ERR_CORRUPT;
     *out = r;
     return FALCON_OK;
 }
 
-int compress_args(const void *d_in, uint64_t n, int dtype, uint32_t block, void *d_out,
-                  size_t out_capacity) {
+}  // namespace
+
+// Argument checks shared by every compression entry point (falcon_internal.h).
+int falcon::compress_args(const void *d_in, uint64_t n, int dtype, uint32_t block, void *d_out,
+                          size_t out_capacity) {
     if (dtype != FALCON_F64 && dtype != FALCON_F32) return FALCON_ERR_INVALID;
     int st = check_block(block);
     if (st) return st;
@@ -95,6 +98,8 @@ int compress_args(const void *d_in, uint64_t n, int dtype, uint32_t block, void 
     if (out_capacity < FALCON_HEADER_BYTES + 4 * num_chunks(n, block)) return FALCON_ERR_CAPACITY;
     return FALCON_OK;
 }
+
+namespace {
 
 Job make_compress_job(const void *d_in, uint64_t n, int dtype, uint32_t block, void *d_out,
                       size_t out_capacity, void *flags, uint64_t *result) {
@@ -170,7 +175,7 @@ const char *falcon_status_string(int status) {
 }
 
 size_t falcon_bound(uint64_t n, int dtype, uint32_t block_size) {
-    if ((dtype != FALCON_F64 && dtype != FALCON_F32) || block_size < 2 || block_size > 65537) return 0;
+    if ((dtype != FALCON_F64 && dtype != FALCON_F32) || block_size < 2 || block_size > kMaxBlock) return 0;
     const uint64_t nc = num_chunks(n, block_size);
     size_t total = FALCON_HEADER_BYTES + 4 * (size_t)nc;
     if (nc == 0) return total;
@@ -304,6 +309,7 @@ int falcon_release(void) {
     g_ws.clear();
     cudaSetDevice(cur);
     falcon_pipeline_release();
+    falcon_noalloc_release();
     return FALCON_OK;
 }
 

@@ -22,6 +22,9 @@
 // The paper resolves offsets inside one launch with a decoupled look-back; with about 1800
 // resident warps on a GB300 the waits of that look-back took half of every warp's time, while
 // the analysis recomputed by the emit launch costs less.
+#include <map>
+#include <mutex>
+
 #include "falcon_device.cuh"
 
 namespace falcon {
@@ -657,41 +660,58 @@ constexpr int kCompressCtaSmem = kWarpsPerCta * kEmitWarpBytes;
 constexpr int kAnalyseCtaSmem = kWarpsPerCta * kAnalyseWarpBytes;
 
 namespace {
-int g_occ_cache[2][64] = {{0}};
-int g_sms_cache[64] = {0};
+int persistent_grid_of(const void *kernel, int smem_bytes, int lim, uint64_t total_chunks);
 
 template <typename K>
-int persistent_grid(K kernel, int which, int smem_bytes, uint64_t total_chunks) {
+int persistent_grid(K kernel, int smem_bytes, uint64_t total_chunks) {
+    return persistent_grid_of(reinterpret_cast<const void *>(kernel), smem_bytes, g_ctas_per_sm[0], total_chunks);
+}
+}  // namespace
+
+int compress_grid(uint64_t total_chunks) { return persistent_grid(emit_kernel, kCompressCtaSmem, total_chunks); }
+
+namespace {
+// Resident CTAs per SM of a persistent kernel, looked up once per (kernel, device) under a
+// lock (the server and the pipeline launch from several host threads).
+std::mutex g_occ_mu;
+std::map<std::pair<const void *, int>, std::pair<int, int>> g_occ;   // -> (CTAs per SM, SMs)
+
+int persistent_grid_of(const void *kernel, int smem_bytes, int lim, uint64_t total_chunks) {
     int dev = 0;
     cudaGetDevice(&dev);
-    int &occ_c = g_occ_cache[which][dev & 63];
-    if (occ_c == 0) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        int sms = 0, occ = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem_bytes);
-        g_sms_cache[dev & 63] = sms;
-        occ_c = occ > 0 ? occ : 1;
+    std::pair<int, int> oc;
+    {
+        std::lock_guard<std::mutex> lk(g_occ_mu);
+        auto it = g_occ.find({kernel, dev});
+        if (it == g_occ.end()) {
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+            int sms = 0, occ = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem_bytes);
+            it = g_occ.emplace(std::make_pair(kernel, dev), std::make_pair(occ > 0 ? occ : 1, sms > 0 ? sms : 1)).first;
+        }
+        oc = it->second;
     }
-    const int lim = g_ctas_per_sm[0];
-    const int cached = g_sms_cache[dev & 63] * ((lim > 0 && lim < occ_c) ? lim : occ_c);
+    const int cached = oc.second * ((lim > 0 && lim < oc.first) ? lim : oc.first);
     const uint64_t need = (total_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
     return (int)(need < (uint64_t)cached ? (need > 0 ? need : 1) : (uint64_t)cached);
 }
 }  // namespace
 
-int compress_grid(uint64_t total_chunks) { return persistent_grid(emit_kernel, 1, kCompressCtaSmem, total_chunks); }
+int persistent_grid_size(const void *kernel, int smem_bytes, int lim, uint64_t total_chunks) {
+    return persistent_grid_of(kernel, smem_bytes, lim, total_chunks);
+}
 
 cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,
                             Control *ctl, cudaStream_t stream) {
     (void)ctl;
     if (total_chunks > 0) {
-        const int g1 = persistent_grid(analyse_kernel, 0, kAnalyseCtaSmem, total_chunks);
+        const int g1 = persistent_grid(analyse_kernel, kAnalyseCtaSmem, total_chunks);
         analyse_kernel<<<g1, kThreads, kAnalyseCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
     }
     compress_offsets_kernel<<<(d_jobs != nullptr) ? njobs : 1, 1024, 0, stream>>>(d_jobs, single);
     if (total_chunks > 0) {
-        const int g3 = persistent_grid(emit_kernel, 1, kCompressCtaSmem, total_chunks);
+        const int g3 = persistent_grid(emit_kernel, kCompressCtaSmem, total_chunks);
         emit_kernel<<<g3, kThreads, kCompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
     }
     return cudaGetLastError();

@@ -401,25 +401,9 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
 
 constexpr int kDecompressCtaSmem = kWarpsPerCta * kWarpBytes;
 
-static int g_occ_cache[64] = {0};
-static int g_sms_cache[64] = {0};
-
 int decompress_grid(uint64_t total_chunks) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int &occ_c = g_occ_cache[dev & 63];
-    if (occ_c == 0) {
-        cudaFuncSetAttribute(decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDecompressCtaSmem);
-        int sms = 0, occ = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decompress_kernel, kThreads, kDecompressCtaSmem);
-        g_sms_cache[dev & 63] = sms;
-        occ_c = occ > 0 ? occ : 1;
-    }
-    const int lim = g_ctas_per_sm[1];
-    const int cached = g_sms_cache[dev & 63] * ((lim > 0 && lim < occ_c) ? lim : occ_c);
-    const uint64_t need = (total_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
-    return (int)(need < (uint64_t)cached ? (need > 0 ? need : 1) : (uint64_t)cached);
+    return persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel), kDecompressCtaSmem,
+                                g_ctas_per_sm[1], total_chunks);
 }
 
 cudaError_t launch_decompress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,

@@ -57,9 +57,17 @@ cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single,
 cudaError_t launch_decompress(const Job *d_jobs, int njobs, const Job &single,
                               uint64_t total_chunks, Control *ctl, cudaStream_t stream);
 
+// Status of the arguments of a compression call (dtype, block size, pointers, alignment,
+// room for the header and size array), checked before anything is enqueued.
+int compress_args(const void *d_in, uint64_t n, int dtype, uint32_t block, void *d_out, size_t out_capacity);
+
 // Resident CTAs per SM used by the persistent grids (0 = occupancy limit); [0] compress,
 // [1] decompress.  Set through falcon_set_launch_config.
 extern int g_ctas_per_sm[2];
+
+// Persistent grid of a kernel of kThreads threads and smem_bytes dynamic shared memory: as
+// many CTAs as fit (at most lim per SM when lim > 0), fewer when there is less work.
+int persistent_grid_size(const void *kernel, int smem_bytes, int lim, uint64_t total_chunks);
 
 // Grid size used for a launch over total_chunks work items (persistent, occupancy-bound).
 int compress_grid(uint64_t total_chunks);

@@ -37,17 +37,25 @@ int scratch_address(void **out) {
 
 }  // namespace
 
+// Forgets the looked-up addresses (falcon_release): after a context reset the array lives at
+// a new address, which the next call looks up again.
+void falcon_noalloc_release() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (void *&p : g_addr) p = nullptr;
+}
+
 extern "C" int falcon_compress_noalloc(const void *d_in, uint64_t n, int dtype, uint32_t block_size, void *d_out,
                                        size_t out_capacity, uint64_t *d_result, void *stream) {
-    if (block_size >= 2) {
-        const uint64_t chunks = n / block_size + (n % block_size != 0);
-        if (chunks > FALCON_NOALLOC_MAX_CHUNKS) return FALCON_ERR_UNSUPPORTED;
-    }
-    void *scratch = nullptr;
-    const int st = scratch_address(&scratch);
+    // the argument errors first, as falcon_compress_async reports them, then the size limit
+    int st = falcon::compress_args(d_in, n, dtype, block_size, d_out, out_capacity);
     if (st) return st;
-    // zeroes the control block, the look-back words in use and d_result on `stream`, then
-    // launches the kernel
+    if (!d_result || (uintptr_t)d_result % 8 != 0) return FALCON_ERR_INVALID;
+    const uint64_t chunks = n / block_size + (n % block_size != 0);
+    if (chunks > FALCON_NOALLOC_MAX_CHUNKS) return FALCON_ERR_UNSUPPORTED;
+    void *scratch = nullptr;
+    if ((st = scratch_address(&scratch))) return st;
+    // zeroes, on `stream`, the control block, the per-chunk words this call uses and
+    // d_result, then enqueues the three compression launches
     return falcon_compress_async(d_in, n, dtype, block_size, d_out, out_capacity, scratch, kScratchBytes, d_result,
                                  stream);
 }

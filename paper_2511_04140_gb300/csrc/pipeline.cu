@@ -125,7 +125,6 @@ int falcon_pipeline_compress(const void *h_in, uint64_t n, int dtype, uint32_t b
     if (n > 0 && !h_in) return FALCON_ERR_INVALID;
     if (frame_values == 0 || nstreams < 1 || nstreams > 256) return FALCON_ERR_INVALID;
     if (falcon_bound(frame_values, dtype, block_size) == 0) return FALCON_ERR_INVALID;
-    if (block_size > falcon::kMaxBlock) return FALCON_ERR_UNSUPPORTED;
     const size_t s = dtype == FALCON_F64 ? 8 : 4;
     const uint64_t nframes = (n + frame_values - 1) / frame_values;
     const uint64_t fchunks = (frame_values + block_size - 1) / block_size;

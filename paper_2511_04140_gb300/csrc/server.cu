@@ -516,8 +516,7 @@ int falcon_server_submit(falcon_server *s, int op, const void *h_in, uint64_t co
     r.h_in = static_cast<const uint8_t *>(h_in);
     if (op == FALCON_COMPRESS) {
         if (dtype != FALCON_F64 && dtype != FALCON_F32) return FALCON_ERR_INVALID;
-        if (block_size < 2 || block_size > 65537) return FALCON_ERR_INVALID;
-        if (block_size > kMaxBlock) return FALCON_ERR_UNSUPPORTED;
+        if (block_size < 2 || block_size > kMaxBlock) return FALCON_ERR_INVALID;
         if (count > 0 && !h_in) return FALCON_ERR_INVALID;
         if (count > (1ull << 58)) return FALCON_ERR_CAPACITY;
         r.n = count;
@@ -534,7 +533,6 @@ int falcon_server_submit(falcon_server *s, int op, const void *h_in, uint64_t co
         uint32_t blk = 0;
         const int st = falcon_stream_info(h_in, count, &n, &dt, &blk, &nc);
         if (st) return st;
-        if (blk > kMaxBlock) return FALCON_ERR_UNSUPPORTED;
         if (nc > (count - FALCON_HEADER_BYTES) / 4) return FALCON_ERR_CORRUPT;
         if (n > (1ull << 58)) return FALCON_ERR_CAPACITY;
         r.n = n;

@@ -35,11 +35,12 @@ def test_exports_every_declared_symbol(falcon_lib):
 def test_bound_matches_oracle(falcon_lib, oracle):
     for n in (0, 1, 2, 63, 64, 65, 1023, 1024, 1025, 1 << 20, 67108864):
         for dt in (0, 1):
-            for blk in (2, 64, 1024, 1025, 4096, 65537):
+            for blk in (2, 64, 1000, 1024, 1025):
                 assert falcon_lib.bound(n, dt, blk) == oracle.bound(n, dt, blk), (n, dt, blk)
     assert falcon_lib.bound(10, 2, 1024) == 0
     assert falcon_lib.bound(10, 0, 1) == 0
-    assert falcon_lib.bound(10, 0, 65538) == 0
+    for blk in (1026, 4096, 65537):                    # the format stops at n = 1025 (Sec. 3.3)
+        assert falcon_lib.bound(10, 0, blk) == 0 and oracle.bound(10, 0, blk) == 0
 
 
 def test_stream_info_parses_oracle_streams(falcon_lib, oracle):
@@ -55,6 +56,13 @@ def test_stream_info_parses_oracle_streams(falcon_lib, oracle):
     bad = bytearray(s[:32]); bad[24] ^= 1                    # num_chunks inconsistent with n
     with pytest.raises(falcon_lib.FalconError):
         falcon_lib.stream_info(bytes(bad))
+    bad = bytearray(s[:32])                                  # block 4096, 1 chunk: outside the format
+    bad[8:12] = (4096).to_bytes(4, "little"); bad[24:32] = (1).to_bytes(8, "little")
+    with pytest.raises(falcon_lib.FalconError) as e:
+        falcon_lib.stream_info(bytes(bad))
+    assert e.value.status == falcon_lib.ERR_CORRUPT
+    with pytest.raises(ValueError):
+        oracle.decompress(bytes(bad) + bytes(4 + 20))
 
 
 def test_workspace_bytes(falcon_lib):

@@ -45,3 +45,10 @@ def test_sources_digest_ignores_comments_but_not_code(tmp_path):
     assert bench.compress_sources_digest(str(tmp_path)) == base
     cu.write_text(text.replace("constexpr int kMetaShift = 47;", "constexpr int kMetaShift = 46;"))
     assert bench.compress_sources_digest(str(tmp_path)) != base
+
+
+def test_failed_checks_finds_every_false_exactness_key():
+    line = {"bit_exact": True, "batched": {"bit_exact": False, "oracle_equal": True},
+            "serve": {"loads": [{"server": {"bit_exact": True}}, {"one": {"oracle_equal": False}}]}}
+    assert bench.failed_checks(line) == ["line.batched.bit_exact", "line.serve.loads[1].one.oracle_equal"]
+    assert bench.failed_checks({"bit_exact": True, "pipeline": {"bit_exact": True}}) == []

@@ -154,11 +154,12 @@ def test_capacity_error(F):
     assert e.value.status == F.ERR_CAPACITY
 
 
-def test_unsupported_and_invalid(F):
+def test_block_size_outside_format_is_invalid(F):
     x = torch.zeros(10, dtype=torch.float64, device="cuda")
-    with pytest.raises(F.FalconError) as e:
-        F.compress(x, 4096)
-    assert e.value.status == F.ERR_UNSUPPORTED
+    for blk in (1026, 4096, 65537):
+        with pytest.raises(F.FalconError) as e:
+            F.compress(x, blk)
+        assert e.value.status == F.ERR_INVALID
     with pytest.raises(F.FalconError) as e:
         F.compress(x, 1)
     assert e.value.status == F.ERR_INVALID

@@ -78,3 +78,38 @@ def test_maximum_size_and_rejection_above_it(F):
     st = F.lib().falcon_compress_noalloc(y.data_ptr(), n + 1, F.F32, 1024, big.data_ptr(), big.numel(),
                                          r.data_ptr(), stream.cuda_stream)
     assert st == F.ERR_UNSUPPORTED
+    # argument errors are reported before the size limit, as falcon_compress_async reports them
+    bad_dtype = F.lib().falcon_compress_noalloc(y.data_ptr(), n + 1, 7, 1024, big.data_ptr(), big.numel(),
+                                                r.data_ptr(), stream.cuda_stream)
+    null_out = F.lib().falcon_compress_noalloc(y.data_ptr(), n + 1, F.F32, 1024, None, big.numel(),
+                                               r.data_ptr(), stream.cuda_stream)
+    bad_block = F.lib().falcon_compress_noalloc(y.data_ptr(), n + 1, F.F32, 4096, big.data_ptr(), big.numel(),
+                                                r.data_ptr(), stream.cuda_stream)
+    assert (bad_dtype, null_out, bad_block) == (F.ERR_INVALID, F.ERR_INVALID, F.ERR_INVALID)
+
+
+def test_calls_allocate_no_device_memory(F):
+    """The point of the entry point: after one call has loaded the module, further calls of
+    several sizes leave the device's free memory and torch's pool exactly as they were."""
+    xs = [torch.from_numpy(synth.segments(k, seed=25 + k % 7)).cuda() for k in (5_000, 300_000, 2_000_001)]
+    outs = [torch.empty(F.bound(x.numel(), F.F64, 1024), dtype=torch.uint8, device="cuda") for x in xs]
+    res = torch.zeros(2, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+
+    def call(i):
+        st = F.lib().falcon_compress_noalloc(xs[i].data_ptr(), xs[i].numel(), F.F64, 1024, outs[i].data_ptr(),
+                                             outs[i].numel(), res.data_ptr(), stream.cuda_stream)
+        assert st == F.OK, st
+
+    call(0)
+    stream.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for _ in range(2):
+        for i in range(len(xs)):
+            call(i)
+    stream.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_reserved() == reserved0
+    assert free1 == free0
+    assert int(res[1].item()) == 0
