@@ -43,6 +43,13 @@
  *       (in FP64), round trip and decode are fl32((float)g / (float)10^alpha).
  *   R16 block sizes: 2 <= B <= 1025 (Sec. 3.3's n = 64k + 1 with the implementation's
  *       n = 1025 as the largest chunk).
+ *   R17 the ablation variants of Sec. 5.4.2 (Fig. 12b) change one step each and keep the
+ *       record layout, so the one decoder reads all of them:
+ *         Fal._Sparse / Fal._Dense: every row of M^T stored sparse / dense;
+ *         Fal._Elf: the decimal place of a value is the trial-and-error one of Sec. 1, the
+ *         first i >= 0 with v (x) 10^i == floor(v (x) 10^i), enumerated within Alg. 2's
+ *         bounds (beta <= 15, alpha <= 22; FP32 7 and 10), none found = exception; the
+ *         chunk's Case decision (Eq. 4) and the R6 round-trip check are unchanged.
  *
  * Stream layout (little-endian):
  *   0  "FLCN"  4  version=1 (u8)  5  dtype (u8: 0=f64, 1=f32)  6  reserved u16 = 0
@@ -193,6 +200,44 @@ void oracle_dp_ds_f32(float v, int *alpha, int *beta)
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Fal._Elf's decimal place (Sec. 1 trial-and-error, Sec. 5.4.2 ablation; R17): the first */
+/* i with v (x) 10^i an integer.  1.11 gives 3 (1.11 (x) 10^2 = 111.00000000000001).     */
+/* ------------------------------------------------------------------------------------ */
+void oracle_dp_elf_f64(double v, int *alpha, int *beta)
+{
+    if (oracle_is_special_f64(v)) { *alpha = 23; *beta = 16; return; }   /* R1 */
+    if (v == 0.0) { *alpha = 0; *beta = 0; return; }
+    int a = 0;
+    int b = a + oracle_floor_log10_f64(fabs(v)) + 1;
+    while (b <= 15 && a <= 22) {
+        double x = v * oracle_pow10_f64(a);                             /* v (x) 10^i */
+        if (x == floor(x)) break;                                       /* integral */
+        a = a + 1;
+        b = b + 1;
+    }
+    if (a > 22 || b > 15) { a = 23; b = 16; }
+    *alpha = a;
+    *beta = b;
+}
+
+void oracle_dp_elf_f32(float v, int *alpha, int *beta)
+{
+    if (oracle_is_special_f32(v)) { *alpha = 11; *beta = 8; return; }
+    if (v == 0.0f) { *alpha = 0; *beta = 0; return; }
+    int a = 0;
+    int b = a + oracle_floor_log10_f32(fabsf(v)) + 1;
+    while (b <= 7 && a <= 10) {
+        float x = v * oracle_pow10_f32(a);                              /* FP32 multiply */
+        if (x == floorf(x)) break;
+        a = a + 1;
+        b = b + 1;
+    }
+    if (a > 10 || b > 7) { a = 11; b = 8; }
+    *alpha = a;
+    *beta = b;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Zigzag (Eq. 5): Zigzag(x) = (x << 1) xor (x >> 63), arithmetic shift (R7).           */
 /* ------------------------------------------------------------------------------------ */
 uint64_t oracle_zigzag64(uint64_t x)
@@ -218,9 +263,9 @@ uint32_t oracle_unzigzag32(uint32_t z)
 /* G = {g_1..g_m} as raw 64-bit words (FP32: low 32 bits).                               */
 /* Returns the number of R6 firings (values that failed the Case-1 round trip).        */
 /* ------------------------------------------------------------------------------------ */
-int oracle_chunk_transform(const void *vals, uint32_t m, int dtype,
-                           int *alpha_max_out, int *beta_hat_out, int *case1_out,
-                           uint64_t *g)
+static int chunk_transform_with(const void *vals, uint32_t m, int dtype, int elf,
+                                int *alpha_max_out, int *beta_hat_out, int *case1_out,
+                                uint64_t *g)
 {
     int r6_firings = 0;
     if (dtype == OR_F64) {
@@ -231,7 +276,8 @@ int oracle_chunk_transform(const void *vals, uint32_t m, int dtype,
         double v_max = 0.0;
         for (uint32_t i = 0; i < m; ++i) {
             int a, b;
-            oracle_dp_ds_f64(v[i], &a, &b);
+            if (elf) oracle_dp_elf_f64(v[i], &a, &b);
+            else oracle_dp_ds_f64(v[i], &a, &b);
             if (a > alpha_max) alpha_max = a;
             if (a > 22 || b > 15) any_exception = 1;
         }
@@ -275,7 +321,8 @@ int oracle_chunk_transform(const void *vals, uint32_t m, int dtype,
         int any_exception = 0;
         for (uint32_t i = 0; i < m; ++i) {
             int a, b;
-            oracle_dp_ds_f32(v[i], &a, &b);
+            if (elf) oracle_dp_elf_f32(v[i], &a, &b);
+            else oracle_dp_ds_f32(v[i], &a, &b);
             if (a > alpha_max) alpha_max = a;
             if (a > 10 || b > 7) any_exception = 1;
         }
@@ -314,6 +361,21 @@ int oracle_chunk_transform(const void *vals, uint32_t m, int dtype,
     return r6_firings;
 }
 
+int oracle_chunk_transform(const void *vals, uint32_t m, int dtype,
+                           int *alpha_max_out, int *beta_hat_out, int *case1_out,
+                           uint64_t *g)
+{
+    return chunk_transform_with(vals, m, dtype, 0, alpha_max_out, beta_hat_out, case1_out, g);
+}
+
+/* The same with Fal._Elf's decimal place (R17). */
+int oracle_chunk_transform_elf(const void *vals, uint32_t m, int dtype,
+                               int *alpha_max_out, int *beta_hat_out, int *case1_out,
+                               uint64_t *g)
+{
+    return chunk_transform_with(vals, m, dtype, 1, alpha_max_out, beta_hat_out, case1_out, g);
+}
+
 /* Eq. 5: z_1 = g_1, z_i = Zigzag(g_i - g_{i-1}) for i > 1 (modulo 2^64 / 2^32). */
 void oracle_delta_zigzag(const uint64_t *g, uint32_t m, int dtype, uint64_t *z)
 {
@@ -344,9 +406,13 @@ static int plane_bit(const uint64_t *z, uint32_t m, uint32_t c, int p)
     return (int)((z[idx] >> p) & 1u);
 }
 
+/* Row storage of the record encoder: the adaptive choice of Sec. 3.3, or every row sparse
+   (Fal._Sparse) or dense (Fal._Dense) as in the ablation of Sec. 5.4.2 (R17). */
+enum { OR_STORE_ADAPTIVE = 0, OR_STORE_SPARSE = 1, OR_STORE_DENSE = 2 };
+
 /* Encodes one record; returns its byte length or 0 if it does not fit in cap. */
-size_t oracle_encode_z(const uint64_t *z, uint32_t m, int dtype, int alpha_max, int beta_hat,
-                       uint8_t *out, size_t cap)
+size_t oracle_encode_z_storage(const uint64_t *z, uint32_t m, int dtype, int alpha_max, int beta_hat,
+                               int storage, uint8_t *out, size_t cap)
 {
     const int width = (dtype == OR_F64) ? 64 : 32;
     const int z1_bytes = (dtype == OR_F64) ? 8 : 4;
@@ -385,6 +451,8 @@ size_t oracle_encode_z(const uint64_t *z, uint32_t m, int dtype, int alpha_max, 
             if (byte == 0) ++lambda;              /* zero byte */
         }
         int sparse = lambda > cols / 64;          /* Sec. 3.3 criterion, tie -> dense (R10) */
+        if (storage == OR_STORE_SPARSE) sparse = 1;
+        if (storage == OR_STORE_DENSE) sparse = 0;
         /* flag: the last w bits of the flag bytes, row 1 first, MSB-first (R9) */
         uint32_t bitpos = flag_bytes * 8 - (uint32_t)w + (uint32_t)(r - 1);
         if (!sparse) out[flag_pos + bitpos / 8] |= (uint8_t)(0x80u >> (bitpos % 8));
@@ -407,18 +475,40 @@ size_t oracle_encode_z(const uint64_t *z, uint32_t m, int dtype, int alpha_max, 
     return pos;
 }
 
-/* One chunk: Eq. 4 -> Eq. 5 -> Sec. 3.3. Returns the record length, 0 on overflow. */
-size_t oracle_encode_chunk(const void *vals, uint32_t m, int dtype, uint8_t *out, size_t cap)
+size_t oracle_encode_z(const uint64_t *z, uint32_t m, int dtype, int alpha_max, int beta_hat,
+                       uint8_t *out, size_t cap)
 {
+    return oracle_encode_z_storage(z, m, dtype, alpha_max, beta_hat, OR_STORE_ADAPTIVE, out, cap);
+}
+
+/* Codec variants (R17): Falcon itself and the three ablations of Sec. 5.4.2. */
+enum { OR_VARIANT_FALCON = 0, OR_VARIANT_SPARSE = 1, OR_VARIANT_DENSE = 2, OR_VARIANT_ELF = 3 };
+
+/* One chunk of a variant: Eq. 4 -> Eq. 5 -> Sec. 3.3. Returns the record length, 0 on
+   overflow or an unknown variant. */
+size_t oracle_encode_chunk_variant(const void *vals, uint32_t m, int dtype, int variant,
+                                   uint8_t *out, size_t cap)
+{
+    if (variant < OR_VARIANT_FALCON || variant > OR_VARIANT_ELF) return 0;
     uint64_t *g = (uint64_t *)malloc(sizeof(uint64_t) * (m ? m : 1));
     uint64_t *z = (uint64_t *)malloc(sizeof(uint64_t) * (m ? m : 1));
     int alpha_max, beta_hat, case1;
-    oracle_chunk_transform(vals, m, dtype, &alpha_max, &beta_hat, &case1, g);
+    if (variant == OR_VARIANT_ELF) oracle_chunk_transform_elf(vals, m, dtype, &alpha_max, &beta_hat, &case1, g);
+    else oracle_chunk_transform(vals, m, dtype, &alpha_max, &beta_hat, &case1, g);
     oracle_delta_zigzag(g, m, dtype, z);
-    size_t len = oracle_encode_z(z, m, dtype, alpha_max, beta_hat, out, cap);
+    int storage = OR_STORE_ADAPTIVE;
+    if (variant == OR_VARIANT_SPARSE) storage = OR_STORE_SPARSE;
+    if (variant == OR_VARIANT_DENSE) storage = OR_STORE_DENSE;
+    size_t len = oracle_encode_z_storage(z, m, dtype, alpha_max, beta_hat, storage, out, cap);
     free(g);
     free(z);
     return len;
+}
+
+/* One chunk: Eq. 4 -> Eq. 5 -> Sec. 3.3. Returns the record length, 0 on overflow. */
+size_t oracle_encode_chunk(const void *vals, uint32_t m, int dtype, uint8_t *out, size_t cap)
+{
+    return oracle_encode_chunk_variant(vals, m, dtype, OR_VARIANT_FALCON, out, cap);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -444,19 +534,27 @@ size_t oracle_bound(uint64_t n, int dtype, uint32_t block)
     return total;
 }
 
+/* Largest record of a variant: a row is at most cols/8 bytes (dense), except under
+   Fal._Sparse, where a row without zero bytes takes its bitmap as well (cols/64 + cols/8). */
+size_t oracle_bound_variant(uint64_t n, int dtype, uint32_t block, int variant)
+{
+    size_t total = oracle_bound(n, dtype, block);
+    if (total == 0 || variant != 1) return total;          /* 1 = Fal._Sparse */
+    const int width = (dtype == OR_F64) ? 64 : 32;
+    const uint64_t nc = num_chunks_of(n, block);
+    if (nc == 0) return total;
+    total += (size_t)(nc - 1) * (size_t)width * (chunk_cols(block) / 64);
+    total += (size_t)width * (chunk_cols((uint32_t)(n - (nc - 1) * (uint64_t)block)) / 64);
+    return total;
+}
+
 static void put_u32(uint8_t *p, uint32_t x) { for (int k = 0; k < 4; ++k) p[k] = (uint8_t)(x >> (8 * k)); }
 static void put_u64(uint8_t *p, uint64_t x) { for (int k = 0; k < 8; ++k) p[k] = (uint8_t)(x >> (8 * k)); }
 static uint32_t get_u32(const uint8_t *p) { uint32_t x = 0; for (int k = 3; k >= 0; --k) x = (x << 8) | p[k]; return x; }
 static uint64_t get_u64(const uint8_t *p) { uint64_t x = 0; for (int k = 7; k >= 0; --k) x = (x << 8) | p[k]; return x; }
 
-int oracle_compress(const void *in, uint64_t n, int dtype, uint32_t block,
-                    uint8_t *out, size_t cap, size_t *out_bytes)
+static void put_header(uint8_t *out, uint64_t n, int dtype, uint32_t block, uint64_t nc)
 {
-    if ((dtype != OR_F64 && dtype != OR_F32) || block < 2 || block > OR_MAX_BLOCK) return OR_ERR_INVALID;
-    const size_t s = (dtype == OR_F64) ? 8 : 4;
-    const uint64_t nc = num_chunks_of(n, block);
-    const size_t data_start = OR_HEADER_BYTES + 4 * (size_t)nc;
-    if (cap < data_start) return OR_ERR_CAPACITY;
     memcpy(out, "FLCN", 4);
     out[4] = 1;
     out[5] = (uint8_t)dtype;
@@ -465,17 +563,36 @@ int oracle_compress(const void *in, uint64_t n, int dtype, uint32_t block,
     put_u32(out + 12, 0);
     put_u64(out + 16, n);
     put_u64(out + 24, nc);
+}
+
+int oracle_compress_variant(const void *in, uint64_t n, int dtype, uint32_t block, int variant,
+                            uint8_t *out, size_t cap, size_t *out_bytes)
+{
+    if ((dtype != OR_F64 && dtype != OR_F32) || block < 2 || block > OR_MAX_BLOCK) return OR_ERR_INVALID;
+    if (variant < OR_VARIANT_FALCON || variant > OR_VARIANT_ELF) return OR_ERR_INVALID;
+    const size_t s = (dtype == OR_F64) ? 8 : 4;
+    const uint64_t nc = num_chunks_of(n, block);
+    const size_t data_start = OR_HEADER_BYTES + 4 * (size_t)nc;
+    if (cap < data_start) return OR_ERR_CAPACITY;
+    put_header(out, n, dtype, block, nc);
     size_t pos = data_start;
     for (uint64_t c = 0; c < nc; ++c) {
         uint64_t first = c * block;
         uint32_t m = (uint32_t)((n - first) < block ? (n - first) : block);
-        size_t len = oracle_encode_chunk((const uint8_t *)in + first * s, m, dtype, out + pos, cap - pos);
+        size_t len = oracle_encode_chunk_variant((const uint8_t *)in + first * s, m, dtype, variant, out + pos,
+                                                 cap - pos);
         if (len == 0) return OR_ERR_CAPACITY;
         put_u32(out + OR_HEADER_BYTES + 4 * c, (uint32_t)len);
         pos += len;
     }
     *out_bytes = pos;
     return OR_OK;
+}
+
+int oracle_compress(const void *in, uint64_t n, int dtype, uint32_t block,
+                    uint8_t *out, size_t cap, size_t *out_bytes)
+{
+    return oracle_compress_variant(in, n, dtype, block, OR_VARIANT_FALCON, out, cap, out_bytes);
 }
 
 /* Parses a stream header. */
@@ -606,4 +723,159 @@ int oracle_decompress(const uint8_t *in, size_t in_bytes, void *out, size_t out_
     }
     *n_out = n;
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Multi-threaded drivers (for timing on all host cores and for checking large inputs):  */
+/* threads take contiguous chunk ranges and call the unchanged per-chunk functions above; */
+/* the records are joined in chunk order, so the stream is the single-threaded one.     */
+/* ------------------------------------------------------------------------------------ */
+#include <pthread.h>
+
+typedef struct {
+    const uint8_t *in;
+    uint64_t n, c0, c1;
+    int dtype, variant;
+    uint32_t block;
+    uint8_t *sizes;          /* the stream's size array */
+    uint8_t *buf;            /* private records of chunks c0..c1 */
+    size_t cap, len;
+    int status;
+    uint8_t *dst;            /* phase 2: where the records go */
+} mt_comp;
+
+static void *mt_comp_encode(void *arg)
+{
+    mt_comp *t = (mt_comp *)arg;
+    const size_t s = (t->dtype == OR_F64) ? 8 : 4;
+    size_t pos = 0;
+    for (uint64_t c = t->c0; c < t->c1; ++c) {
+        uint64_t first = c * t->block;
+        uint32_t m = (uint32_t)((t->n - first) < t->block ? (t->n - first) : t->block);
+        size_t len = oracle_encode_chunk_variant(t->in + first * s, m, t->dtype, t->variant, t->buf + pos,
+                                                 t->cap - pos);
+        if (len == 0) { t->status = OR_ERR_CAPACITY; return NULL; }
+        put_u32(t->sizes + 4 * c, (uint32_t)len);
+        pos += len;
+    }
+    t->len = pos;
+    return NULL;
+}
+
+static void *mt_comp_place(void *arg)
+{
+    mt_comp *t = (mt_comp *)arg;
+    memcpy(t->dst, t->buf, t->len);
+    return NULL;
+}
+
+int oracle_compress_mt(const void *in, uint64_t n, int dtype, uint32_t block, int variant, int nthreads,
+                       uint8_t *out, size_t cap, size_t *out_bytes)
+{
+    if ((dtype != OR_F64 && dtype != OR_F32) || block < 2 || block > OR_MAX_BLOCK) return OR_ERR_INVALID;
+    if (variant < OR_VARIANT_FALCON || variant > OR_VARIANT_ELF || nthreads < 1) return OR_ERR_INVALID;
+    const uint64_t nc = num_chunks_of(n, block);
+    const size_t data_start = OR_HEADER_BYTES + 4 * (size_t)nc;
+    if (cap < data_start) return OR_ERR_CAPACITY;
+    if ((uint64_t)nthreads > nc) nthreads = nc ? (int)nc : 1;
+    mt_comp *ts = (mt_comp *)calloc((size_t)nthreads, sizeof(mt_comp));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    int st = OR_OK;
+    for (int i = 0; i < nthreads; ++i) {
+        mt_comp *t = &ts[i];
+        t->in = (const uint8_t *)in; t->n = n; t->dtype = dtype; t->variant = variant; t->block = block;
+        t->c0 = nc * (uint64_t)i / (uint64_t)nthreads;
+        t->c1 = nc * (uint64_t)(i + 1) / (uint64_t)nthreads;
+        t->sizes = out + OR_HEADER_BYTES;
+        t->cap = 0;
+        for (uint64_t c = t->c0; c < t->c1; ++c) {
+            uint64_t first = c * block;
+            t->cap += record_bound((uint32_t)((n - first) < block ? (n - first) : block), dtype);
+        }
+        t->buf = (uint8_t *)malloc(t->cap ? t->cap : 1);
+        if (!t->buf) st = OR_ERR_CAPACITY;
+    }
+    if (st == OR_OK) {
+        for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, mt_comp_encode, &ts[i]);
+        for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+        size_t pos = data_start;
+        for (int i = 0; i < nthreads; ++i) {
+            if (ts[i].status) st = ts[i].status;
+            ts[i].dst = out + pos;
+            pos += ts[i].len;
+        }
+        if (st == OR_OK && pos > cap) st = OR_ERR_CAPACITY;
+        if (st == OR_OK) {
+            for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, mt_comp_place, &ts[i]);
+            for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+            put_header(out, n, dtype, block, nc);
+            *out_bytes = pos;
+        }
+    }
+    for (int i = 0; i < nthreads; ++i) free(ts[i].buf);
+    free(ts);
+    free(th);
+    return st;
+}
+
+typedef struct {
+    const uint8_t *in;
+    const size_t *offs;      /* record offset of every chunk */
+    uint64_t n, c0, c1;
+    uint32_t block;
+    int dtype, status;
+    uint8_t *out;
+} mt_dec;
+
+static void *mt_dec_run(void *arg)
+{
+    mt_dec *t = (mt_dec *)arg;
+    const size_t s = (t->dtype == OR_F64) ? 8 : 4;
+    for (uint64_t c = t->c0; c < t->c1; ++c) {
+        uint64_t first = c * t->block;
+        uint32_t m = (uint32_t)((t->n - first) < t->block ? (t->n - first) : t->block);
+        int st = oracle_decode_chunk(t->in + t->offs[c], t->offs[c + 1] - t->offs[c], m, t->dtype, t->out + first * s);
+        if (st != OR_OK) { t->status = st; return NULL; }
+    }
+    return NULL;
+}
+
+int oracle_decompress_mt(const uint8_t *in, size_t in_bytes, void *out, size_t out_cap_bytes, uint64_t *n_out,
+                         int nthreads)
+{
+    uint64_t n, nc;
+    int dtype;
+    uint32_t block;
+    if (nthreads < 1) return OR_ERR_INVALID;
+    int st = oracle_stream_info(in, in_bytes, &n, &dtype, &block, &nc);
+    if (st != OR_OK) return st;
+    const size_t s = (dtype == OR_F64) ? 8 : 4;
+    if (n > out_cap_bytes / s) return OR_ERR_CAPACITY;
+    if (nc > (in_bytes - OR_HEADER_BYTES) / 4) return OR_ERR_CORRUPT;
+    size_t *offs = (size_t *)malloc(sizeof(size_t) * (size_t)(nc + 1));
+    if (!offs) return OR_ERR_CAPACITY;
+    offs[0] = OR_HEADER_BYTES + 4 * (size_t)nc;
+    for (uint64_t c = 0; c < nc; ++c) {
+        uint32_t len = get_u32(in + OR_HEADER_BYTES + 4 * c);
+        if (len > in_bytes - offs[c]) { free(offs); return OR_ERR_CORRUPT; }
+        offs[c + 1] = offs[c] + len;
+    }
+    if ((uint64_t)nthreads > nc) nthreads = nc ? (int)nc : 1;
+    mt_dec *ts = (mt_dec *)calloc((size_t)nthreads, sizeof(mt_dec));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    for (int i = 0; i < nthreads; ++i) {
+        mt_dec *t = &ts[i];
+        t->in = in; t->offs = offs; t->n = n; t->block = block; t->dtype = dtype; t->out = (uint8_t *)out;
+        t->c0 = nc * (uint64_t)i / (uint64_t)nthreads;
+        t->c1 = nc * (uint64_t)(i + 1) / (uint64_t)nthreads;
+        pthread_create(&th[i], NULL, mt_dec_run, t);
+    }
+    for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+    st = OR_OK;
+    for (int i = 0; i < nthreads; ++i) if (ts[i].status) { st = ts[i].status; break; }
+    free(ts);
+    free(th);
+    free(offs);
+    if (st == OR_OK) *n_out = n;
+    return st;
 }

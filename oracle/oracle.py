@@ -24,6 +24,8 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 
 F64, F32 = 0, 1
 OK, ERR_INVALID, ERR_CAPACITY, ERR_CORRUPT = 0, 1, 2, 3
+# codec variants: Falcon and the ablations of Sec. 5.4.2 (Fal._Sparse, Fal._Dense, Fal._Elf)
+FALCON, SPARSE, DENSE, ELF = 0, 1, 2, 3
 
 _lock = threading.Lock()
 _lib = None
@@ -34,7 +36,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-pthread",
                                "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -56,6 +58,20 @@ def lib():
             L.oracle_floor_log10_f32.argtypes = [c.c_float]
             L.oracle_dp_ds_f64.argtypes = [c.c_double, c.POINTER(c.c_int), c.POINTER(c.c_int)]
             L.oracle_dp_ds_f32.argtypes = [c.c_float, c.POINTER(c.c_int), c.POINTER(c.c_int)]
+            L.oracle_dp_elf_f64.argtypes = [c.c_double, c.POINTER(c.c_int), c.POINTER(c.c_int)]
+            L.oracle_dp_elf_f32.argtypes = [c.c_float, c.POINTER(c.c_int), c.POINTER(c.c_int)]
+            L.oracle_chunk_transform_elf.argtypes = [c.c_void_p, c.c_uint32, c.c_int,
+                                                     c.POINTER(c.c_int), c.POINTER(c.c_int),
+                                                     c.POINTER(c.c_int), c.c_void_p]
+            L.oracle_encode_z_storage.restype = c.c_size_t
+            L.oracle_encode_z_storage.argtypes = [c.c_void_p, c.c_uint32, c.c_int, c.c_int, c.c_int,
+                                                  c.c_int, c.c_void_p, c.c_size_t]
+            L.oracle_compress_variant.argtypes = [c.c_void_p, c.c_uint64, c.c_int, c.c_uint32, c.c_int,
+                                                  c.c_void_p, c.c_size_t, c.POINTER(c.c_size_t)]
+            L.oracle_compress_mt.argtypes = [c.c_void_p, c.c_uint64, c.c_int, c.c_uint32, c.c_int, c.c_int,
+                                             c.c_void_p, c.c_size_t, c.POINTER(c.c_size_t)]
+            L.oracle_decompress_mt.argtypes = [c.c_void_p, c.c_size_t, c.c_void_p, c.c_size_t,
+                                               c.POINTER(c.c_uint64), c.c_int]
             for name in ("oracle_zigzag64", "oracle_unzigzag64"):
                 getattr(L, name).restype = c.c_uint64
                 getattr(L, name).argtypes = [c.c_uint64]
@@ -74,6 +90,8 @@ def lib():
                                               c.c_size_t]
             L.oracle_decode_chunk.argtypes = [c.c_void_p, c.c_size_t, c.c_uint32, c.c_int,
                                               c.c_void_p]
+            L.oracle_bound_variant.restype = c.c_size_t
+            L.oracle_bound_variant.argtypes = [c.c_uint64, c.c_int, c.c_uint32, c.c_int]
             L.oracle_bound.restype = c.c_size_t
             L.oracle_bound.argtypes = [c.c_uint64, c.c_int, c.c_uint32]
             L.oracle_compress.argtypes = [c.c_void_p, c.c_uint64, c.c_int, c.c_uint32,
@@ -116,6 +134,17 @@ def dp_ds(v, dtype=np.float64):
     return a.value, b.value
 
 
+def dp_elf(v, dtype=np.float64):
+    """Fal._Elf's trial-and-error decimal place (Sec. 1, Sec. 5.4.2) -> (alpha, beta)."""
+    L = lib()
+    a, b = ctypes.c_int(), ctypes.c_int()
+    if dtype == np.float64:
+        L.oracle_dp_elf_f64(float(v), ctypes.byref(a), ctypes.byref(b))
+    else:
+        L.oracle_dp_elf_f32(float(np.float32(v)), ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
 def floor_log10(v, dtype=np.float64) -> int:
     L = lib()
     if dtype == np.float64:
@@ -147,13 +176,14 @@ def unzigzag32(z: int) -> int:
 
 
 # ----------------------------------------------------------------------------- chunk steps
-def chunk_transform(vals: np.ndarray):
-    """Eq. 4 on one chunk -> (alpha_max, beta_hat_max, case1, G as uint64 words)."""
+def chunk_transform(vals: np.ndarray, elf: bool = False):
+    """Eq. 4 on one chunk -> (alpha_max, beta_hat_max, case1, G as uint64 words); elf=True
+    takes Fal._Elf's decimal places."""
     vals = np.ascontiguousarray(vals)
     g = np.zeros(max(len(vals), 1), dtype=np.uint64)
     a, b, c1 = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    lib().oracle_chunk_transform(_ptr(vals), len(vals), _dtype_code(vals), ctypes.byref(a),
-                                 ctypes.byref(b), ctypes.byref(c1), _ptr(g))
+    fn = lib().oracle_chunk_transform_elf if elf else lib().oracle_chunk_transform
+    fn(_ptr(vals), len(vals), _dtype_code(vals), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c1), _ptr(g))
     return a.value, b.value, bool(c1.value), g[:len(vals)]
 
 
@@ -164,11 +194,12 @@ def delta_zigzag(g: np.ndarray, dtype_code: int) -> np.ndarray:
     return z[:len(g)]
 
 
-def encode_z(z: np.ndarray, dtype_code: int, alpha_max: int, beta_hat: int) -> bytes:
+def encode_z(z: np.ndarray, dtype_code: int, alpha_max: int, beta_hat: int, storage: int = 0) -> bytes:
+    """Sec. 3.3 record of Z; storage 0 = adaptive, 1 = every row sparse, 2 = every row dense."""
     z = np.ascontiguousarray(z, dtype=np.uint64)
     cap = 16 + 8 * 64 * (len(z) + 64)
     out = np.zeros(cap, dtype=np.uint8)
-    n = lib().oracle_encode_z(_ptr(z), len(z), dtype_code, alpha_max, beta_hat, _ptr(out), cap)
+    n = lib().oracle_encode_z_storage(_ptr(z), len(z), dtype_code, alpha_max, beta_hat, storage, _ptr(out), cap)
     if n == 0:
         raise RuntimeError("oracle_encode_z overflow")
     return out[:n].tobytes()
@@ -195,20 +226,30 @@ def decode_chunk(rec: bytes, m: int, dtype=np.float64) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------- stream level
-def bound(n: int, dtype_code: int, block: int) -> int:
+def bound(n: int, dtype_code: int, block: int, variant: int = FALCON) -> int:
+    if variant != FALCON:
+        return lib().oracle_bound_variant(n, dtype_code, block, variant)
     return lib().oracle_bound(n, dtype_code, block)
 
 
-def compress(vals: np.ndarray, block: int = 1024) -> bytes:
+def compress(vals: np.ndarray, block: int = 1024, variant: int = FALCON, threads: int = 1) -> bytes:
+    """The stream of `vals`; variant selects Falcon or one of its ablations; threads > 1 runs
+    the multi-threaded driver (same bytes)."""
     vals = np.ascontiguousarray(vals)
     code = _dtype_code(vals)
-    cap = bound(len(vals), code, block)
+    cap = bound(len(vals), code, block, variant)
     if cap == 0:
         raise ValueError("invalid arguments")
-    out = np.zeros(cap, dtype=np.uint8)
+    out = np.empty(cap, dtype=np.uint8)
     nbytes = ctypes.c_size_t()
-    st = lib().oracle_compress(_ptr(vals), len(vals), code, block, _ptr(out), cap,
-                               ctypes.byref(nbytes))
+    if threads > 1:
+        st = lib().oracle_compress_mt(_ptr(vals), len(vals), code, block, variant, threads, _ptr(out), cap,
+                                      ctypes.byref(nbytes))
+    elif variant != FALCON:
+        st = lib().oracle_compress_variant(_ptr(vals), len(vals), code, block, variant, _ptr(out), cap,
+                                           ctypes.byref(nbytes))
+    else:
+        st = lib().oracle_compress(_ptr(vals), len(vals), code, block, _ptr(out), cap, ctypes.byref(nbytes))
     if st != OK:
         raise ValueError(f"oracle_compress status {st}")
     return out[:nbytes.value].tobytes()
@@ -225,7 +266,7 @@ def stream_info(stream: bytes):
     return n.value, dt.value, blk.value, nc.value
 
 
-def decompress_status(stream: bytes):
+def decompress_status(stream: bytes, threads: int = 1):
     """Returns (status, values or None) without raising."""
     buf = np.frombuffer(stream, dtype=np.uint8)
     if len(buf) < 32:
@@ -240,14 +281,17 @@ def decompress_status(stream: bytes):
         return ERR_CORRUPT, None
     out = np.zeros(max(n, 1), dtype=dtype)
     nout = ctypes.c_uint64()
-    st = lib().oracle_decompress(_ptr(buf), len(buf), _ptr(out), n * s, ctypes.byref(nout))
+    if threads > 1:
+        st = lib().oracle_decompress_mt(_ptr(buf), len(buf), _ptr(out), n * s, ctypes.byref(nout), threads)
+    else:
+        st = lib().oracle_decompress(_ptr(buf), len(buf), _ptr(out), n * s, ctypes.byref(nout))
     if st != OK:
         return st, None
     return OK, out[:n]
 
 
-def decompress(stream: bytes) -> np.ndarray:
-    st, out = decompress_status(stream)
+def decompress(stream: bytes, threads: int = 1) -> np.ndarray:
+    st, out = decompress_status(stream, threads)
     if st != OK:
         raise ValueError(f"oracle_decompress status {st}")
     return out

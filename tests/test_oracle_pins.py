@@ -56,6 +56,14 @@ def test_paper_example(oracle, kind, args, expected, cite):
             [int(x) for x in expected[1].split(",")], cite
     elif kind == "bits":
         assert int(args[0]).bit_length() == int(expected[0]), cite
+    elif kind == "elf":
+        assert oracle.dp_elf(float(args[0]))[0] == int(expected[0]), cite
+    elif kind == "chunk_g_elf":
+        vals = np.array([float(x) for x in args[0].split(",")])
+        a, b, case1, g = oracle.chunk_transform(vals, elf=True)
+        assert case1 and a == int(expected[0]), cite
+        assert [int(np.int64(x)) for x in g.view(np.int64)] == \
+            [int(x) for x in expected[1].split(",")], cite
     else:
         raise AssertionError(kind)
 
