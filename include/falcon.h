@@ -127,6 +127,36 @@ int falcon_decompress_async(const void *d_in, size_t in_bytes, const void *h_hea
                             void *d_out, size_t out_capacity_bytes, void *d_workspace,
                             size_t workspace_bytes, uint64_t *d_result, void *stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Codec variants: Falcon and the three ablations of Sec. 5.4.2 (Fig. 12b).  Each changes one
+ * step and keeps the record layout, so falcon_decompress reads every variant's streams:
+ *   FALCON_VARIANT_FALCON  the method itself (what falcon_compress writes);
+ *   FALCON_VARIANT_SPARSE  Fal._Sparse: every row of the transposed bit-plane matrix stored
+ *                          sparse (bitmap + non-zero bytes), whatever its zero-byte count;
+ *   FALCON_VARIANT_DENSE   Fal._Dense: every row stored dense;
+ *   FALCON_VARIANT_ELF     Fal._Elf: a value's decimal place is the trial-and-error one of
+ *                          Sec. 1 (the first i with v (x) 10^i integral, within Alg. 2's bounds
+ *                          alpha <= 22 and beta <= 15; FP32 10 and 7), in place of Alg. 2; the
+ *                          chunk's Case decision and round-trip check are Falcon's.
+ * ------------------------------------------------------------------------------------- */
+typedef enum {
+    FALCON_VARIANT_FALCON = 0,
+    FALCON_VARIANT_SPARSE = 1,
+    FALCON_VARIANT_DENSE = 2,
+    FALCON_VARIANT_ELF = 3
+} falcon_variant;
+
+/* Worst-case stream size of a variant: falcon_bound, except FALCON_VARIANT_SPARSE, whose rows
+ * may each carry their cols/64-byte bitmap on top of cols/8 non-zero bytes.  0 for invalid
+ * arguments. */
+size_t falcon_variant_bound(uint64_t n, int dtype, uint32_t block_size, int variant);
+
+/* falcon_compress_async for a codec variant (same arguments, workspace, d_result and errors;
+ * FALCON_ERR_INVALID for an unknown variant).  Size d_out with falcon_variant_bound. */
+int falcon_compress_variant_async(const void *d_in, uint64_t n, int dtype, uint32_t block_size,
+                                  int variant, void *d_out, size_t out_capacity, void *d_workspace,
+                                  size_t workspace_bytes, uint64_t *d_result, void *stream);
+
 /* Allocation-free compression.  The paper has no counterpart: it is a deployment variant of
  * falcon_compress_async whose scratch (control block and per-chunk words) is a file-scope
  * static device array of the library, sized for FALCON_NOALLOC_MAX_CHUNKS chunks

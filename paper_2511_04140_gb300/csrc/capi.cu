@@ -227,6 +227,27 @@ int falcon_compress(const void *d_in, uint64_t n, int dtype, uint32_t block_size
 int falcon_compress_async(const void *d_in, uint64_t n, int dtype, uint32_t block_size, void *d_out,
                           size_t out_capacity, void *d_workspace, size_t workspace_bytes,
                           uint64_t *d_result, void *stream) {
+    return falcon_compress_variant_async(d_in, n, dtype, block_size, FALCON_VARIANT_FALCON, d_out, out_capacity,
+                                         d_workspace, workspace_bytes, d_result, stream);
+}
+
+size_t falcon_variant_bound(uint64_t n, int dtype, uint32_t block_size, int variant) {
+    if (variant < FALCON_VARIANT_FALCON || variant > FALCON_VARIANT_ELF) return 0;
+    size_t total = falcon_bound(n, dtype, block_size);
+    if (total == 0 || variant != FALCON_VARIANT_SPARSE) return total;
+    const uint64_t nc = num_chunks(n, block_size);
+    if (nc == 0) return total;
+    const size_t W = dtype == FALCON_F64 ? 64 : 32;
+    auto cols = [](uint64_t m) -> size_t { return m <= 1 ? 0 : ((m - 1 + 63) / 64) * 64; };
+    total += (size_t)(nc - 1) * W * (cols(block_size) / 64);
+    total += W * (cols(n - (nc - 1) * (uint64_t)block_size) / 64);
+    return total;
+}
+
+int falcon_compress_variant_async(const void *d_in, uint64_t n, int dtype, uint32_t block_size, int variant,
+                                  void *d_out, size_t out_capacity, void *d_workspace, size_t workspace_bytes,
+                                  uint64_t *d_result, void *stream) {
+    if (variant < FALCON_VARIANT_FALCON || variant > FALCON_VARIANT_ELF) return FALCON_ERR_INVALID;
     int st = compress_args(d_in, n, dtype, block_size, d_out, out_capacity);
     if (st) return st;
     const uint64_t nc = num_chunks(n, block_size);
@@ -238,7 +259,8 @@ int falcon_compress_async(const void *d_in, uint64_t n, int dtype, uint32_t bloc
     if (cudaMemsetAsync(d_workspace, 0, need, s) != cudaSuccess) return FALCON_ERR_CUDA;
     if (cudaMemsetAsync(d_result, 0, 16, s) != cudaSuccess) return FALCON_ERR_CUDA;
     uint8_t *w8 = static_cast<uint8_t *>(d_workspace);
-    const Job j = make_compress_job(d_in, n, dtype, block_size, d_out, out_capacity, w8 + kControlBytes, d_result);
+    Job j = make_compress_job(d_in, n, dtype, block_size, d_out, out_capacity, w8 + kControlBytes, d_result);
+    j.variant = (uint32_t)variant;
     if (launch_compress(nullptr, 1, j, nc, reinterpret_cast<Control *>(d_workspace), s) != cudaSuccess)
         return FALCON_ERR_CUDA;
     return FALCON_OK;

@@ -33,9 +33,18 @@ namespace {
 
 constexpr int kBuf = 8288;                  // one chunk of values / one record (+32 readable)
 constexpr int kScratch = 128;
-constexpr int kEmitWarpBytes = kBuf;               // emit: the plane / record buffer
 constexpr int kAnalyseWarpBytes = kBuf + kScratch;  // analysis: one value buffer
-constexpr int kPlOff = 48;                  // plane words: kPlOff + (W-1-p)*128 + 4*lane
+
+// The emit launch's per-warp plane / record buffer: plane p's words at
+// kPlOff + (W-1-p)*128 + 4*lane.  The record is assembled in place, from byte 0, as the planes
+// are consumed top-down: an adaptive or dense row takes at most the 128 bytes of its slot, so
+// the record never overtakes the plane read next with kPlOff = 48.  Every-row-sparse records
+// (Sec. 5.4.2 ablation) may take 16 + 128 bytes per row and use the wide layout, whose plane
+// slots start past 16 bytes of growth per row.
+template <bool kWide> struct EmitLayout {
+    static constexpr int kPlOff = kWide ? 1072 : 48;
+    static constexpr int kBytes = kPlOff + 64 * 128 + 32;          // + 32 readable past any slot
+};
 
 // Copies len bytes from src to dst inside a warp buffer, dst + 14 <= src (the move goes
 // down): unaligned head and tail bytes singly, the 16-byte aligned middle of the
@@ -174,6 +183,55 @@ __device__ int alpha32(const uint8_t *buf, int lane, uint32_t m, uint32_t vx, in
     return all_pass<false>(buf, lane, m, vx, amax) ? amax : -1;
 }
 
+// Fal._Elf's decimal place of one value (Sec. 1's trial and error, ablation of Sec. 5.4.2):
+// the first a with v (x) 10^a integral, a <= 22 and a + floor(log10|v|) + 1 <= 15 (FP32: 10
+// and 7), else -1 (exception).  The products are IEEE multiplies, as the method defines.
+__device__ __forceinline__ int elf_dp(uint64_t u) {
+    const uint64_t au = u & 0x7FFFFFFFFFFFFFFFull;
+    if (au == 0) return 0;
+    if (is_special(u) || !log10_in_range(au)) return -1;
+    const int atop = min(22, 14 - floor_log10(au));
+    const double v = __longlong_as_double((long long)u);
+    for (int a = 0; a <= atop; ++a) {
+        const double x = __dmul_rn(v, __longlong_as_double((long long)FALCON_P10_F64[a - FALCON_P10_F64_LO]));
+        if (x == floor(x)) return a;
+    }
+    return -1;
+}
+__device__ __forceinline__ int elf_dp(uint32_t u) {
+    const uint32_t au = u & 0x7FFFFFFFu;
+    if (au == 0) return 0;
+    if (is_special(u) || !log10_in_range(au)) return -1;
+    const int atop = min(10, 6 - floor_log10(au));
+    const float v = __uint_as_float(u);
+    for (int a = 0; a <= atop; ++a) {
+        const float x = __fmul_rn(v, __uint_as_float(FALCON_P10_F32[a - FALCON_P10_F32_LO]));
+        if (x == floorf(x)) return a;
+    }
+    return -1;
+}
+
+// Fal._Elf: alpha_max = the largest of the values' Elf decimal places, then Eq. 4's bounds and
+// the R6 round trip at alpha_max, as for Falcon; -1 means Case 2.
+template <bool F64>
+__device__ int alpha_elf(const uint8_t *buf, int lane, uint32_t m, typename Traits<F64>::U vx, int e_max) {
+    using T = Traits<F64>;
+    int amax = (m > 1024u && lane == 31) ? elf_dp(vx) : 0;
+    bool bad = amax < 0;
+#pragma unroll 1
+    for (int k = 0; k < 32; ++k) {
+        if (32u * lane + k < m) {
+            const int a = elf_dp(lane_value<F64>(buf, lane, k));
+            bad |= a < 0;
+            amax = a > amax ? a : amax;
+        }
+    }
+    if (__any_sync(kFull, bad)) return -1;
+    amax = (int)__reduce_max_sync(kFull, (uint32_t)amax);
+    if (amax > T::A_MAX || amax + e_max + 1 > T::B_MAX) return -1;
+    return all_pass<F64>(buf, lane, m, vx, amax) ? amax : -1;
+}
+
 __device__ __forceinline__ void issue_chunk(const Job *jobs, int njobs, const Job &single, uint64_t t,
                                             uint8_t *buf, int lane) {
     const Job &job = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
@@ -301,7 +359,9 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
         } else if (log10_in_range(vmax)) {
             const int e_max = floor_log10(vmax);
             const int atop = min(T::A_MAX, T::B_MAX - 1 - e_max);
-            if (atop >= 0) {
+            if (job.variant == kVariantElf) {
+                alpha = alpha_elf<F64>(buf, lane, m, vx, e_max);
+            } else if (atop >= 0) {
                 // quick rejection: Alg. 2 on the largest magnitude first.  The test reads
                 // only |v|, so it runs on vmax itself, the same in every lane.
                 bool fail;
@@ -363,17 +423,19 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
     __syncwarp();
 
     // ---- 5. storage choice (Sec. 3.3) and record size ------------------------------------------
+    // the ablations of Sec. 5.4.2 force one scheme for every row
+    const bool all_sparse = job.variant == kVariantSparse, all_dense = job.variant == kVariantDense;
     uint32_t cost = 0;
     bool dense_lo = false, dense_hi = false;
     if (lane < w) {                              // plane `lane`
         const uint32_t nz = scratch[lane];
-        const bool sparse = (row_bytes - nz) > cols / 64u;           // tie -> dense (R10)
+        const bool sparse = all_sparse || (!all_dense && (row_bytes - nz) > cols / 64u);   // tie -> dense (R10)
         cost += sparse ? cols / 64u + nz : row_bytes;
         dense_lo = !sparse;
     }
     if (F64 && lane + 32 < w) {                  // plane `lane + 32`
         const uint32_t nz = scratch[lane + 32];
-        const bool sparse = (row_bytes - nz) > cols / 64u;
+        const bool sparse = all_sparse || (!all_dense && (row_bytes - nz) > cols / 64u);
         cost += sparse ? cols / 64u + nz : row_bytes;
         dense_hi = !sparse;
     }
@@ -435,9 +497,10 @@ __device__ __forceinline__ void prefetch_chunk(const Job *jobs, int njobs, const
 // Launch 3, one chunk: G, Z and the plane words again (alpha and w from the analysis), then
 // the record at its offset.  meta / dense: the chunk's workspace words; size: its record size;
 // rel: its record offset relative to the first record.
-template <bool F64>
+template <bool F64, bool kWide>
 __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, unsigned long long meta,
                            unsigned long long dense, uint32_t size, uint64_t rel) {
+    constexpr int kPlOff = EmitLayout<kWide>::kPlOff;
     using T = Traits<F64>;
     using U = typename T::U;
     const uint32_t B = job.block;
@@ -485,8 +548,9 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(gdst) & 15u);
 
     // ---- 6. record in shared memory (in place of the consumed plane words), then global ------
-    // Row r (plane w-r) ends before byte 37 + 128 r of the buffer while the plane read next
-    // starts at kPlOff + (64 - w + r) * 128 >= 48 + 128 r: nothing unread is overwritten.
+    // Row r (plane w-r) ends before byte 37 + 128 r of the buffer (37 + 144 r when every row
+    // is sparse, wide layout) while the plane read next starts at kPlOff + (64 - w + r) * 128
+    // >= kPlOff + 128 r: nothing unread is overwritten.
     if ((uint32_t)lane < hdr) {
         uint32_t byte;
         const int i = lane;
@@ -620,12 +684,13 @@ __device__ __forceinline__ EmitInfo load_info(const Job &job, uint64_t c, int la
 }
 
 // Launch 3: the records (fixed stride per warp; the next chunk's values are prefetched into L2).
+template <bool kWide>
 __global__ void __launch_bounds__(kThreads, 4)
 emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint8_t *wbase = smem + warp * kEmitWarpBytes;
+    uint8_t *wbase = smem + warp * EmitLayout<kWide>::kBytes;
     __shared__ Job s_single;
     if (threadIdx.x == 0) s_single = single;
     __syncthreads();
@@ -648,15 +713,15 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
         const Job &job = job_of(jobs, njobs, s_single, t);
         const uint64_t c = t - job.chunk_begin;
         const uint64_t rel = resolve_pos(info.pos);
-        if (job.dtype == 0) emit_chunk<true>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
-        else emit_chunk<false>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
+        if (job.dtype == 0) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
+        else emit_chunk<false, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
         __syncwarp();
         info = next;
     }
     if (lane == 0) bulk_wait();
 }
 
-constexpr int kCompressCtaSmem = kWarpsPerCta * kEmitWarpBytes;
+template <bool kWide> constexpr int kEmitCtaSmem = kWarpsPerCta * EmitLayout<kWide>::kBytes;
 constexpr int kAnalyseCtaSmem = kWarpsPerCta * kAnalyseWarpBytes;
 
 namespace {
@@ -668,7 +733,7 @@ int persistent_grid(K kernel, int smem_bytes, uint64_t total_chunks) {
 }
 }  // namespace
 
-int compress_grid(uint64_t total_chunks) { return persistent_grid(emit_kernel, kCompressCtaSmem, total_chunks); }
+int compress_grid(uint64_t total_chunks) { return persistent_grid(emit_kernel<false>, kEmitCtaSmem<false>, total_chunks); }
 
 namespace {
 // Resident CTAs per SM of a persistent kernel, looked up once per (kernel, device) under a
@@ -705,14 +770,21 @@ int persistent_grid_size(const void *kernel, int smem_bytes, int lim, uint64_t t
 cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,
                             Control *ctl, cudaStream_t stream) {
     (void)ctl;
+    // the every-row-sparse ablation writes records larger than the plane slots hold
+    const bool wide = d_jobs == nullptr && single.variant == kVariantSparse;
     if (total_chunks > 0) {
         const int g1 = persistent_grid(analyse_kernel, kAnalyseCtaSmem, total_chunks);
         analyse_kernel<<<g1, kThreads, kAnalyseCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
     }
     compress_offsets_kernel<<<(d_jobs != nullptr) ? njobs : 1, 1024, 0, stream>>>(d_jobs, single);
     if (total_chunks > 0) {
-        const int g3 = persistent_grid(emit_kernel, kCompressCtaSmem, total_chunks);
-        emit_kernel<<<g3, kThreads, kCompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
+        if (wide) {
+            const int g3 = persistent_grid(emit_kernel<true>, kEmitCtaSmem<true>, total_chunks);
+            emit_kernel<true><<<g3, kThreads, kEmitCtaSmem<true>, stream>>>(d_jobs, njobs, single, total_chunks);
+        } else {
+            const int g3 = persistent_grid(emit_kernel<false>, kEmitCtaSmem<false>, total_chunks);
+            emit_kernel<false><<<g3, kThreads, kEmitCtaSmem<false>, stream>>>(d_jobs, njobs, single, total_chunks);
+        }
     }
     return cudaGetLastError();
 }

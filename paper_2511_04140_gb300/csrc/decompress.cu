@@ -22,7 +22,9 @@ namespace falcon {
 
 namespace {
 
-constexpr int kBuf = 8256;                  // one record (<= 8211 bytes at a 0..15 phase)
+// one record at a 0..15 byte phase, + 16 readable bytes: an FP64 record is at most
+// 19 + 64 * 144 = 9235 bytes (every row sparse without a zero byte: bitmap + 128 bytes)
+constexpr int kBuf = 9280;
 constexpr int kPlane = 8192 + 128;          // 64 plane slots of 128 bytes + 64 u16 sparse-byte totals
 constexpr int kWarpBytes = kBuf + kPlane;
 
@@ -85,9 +87,11 @@ __device__ __forceinline__ void resolve(const Job *jobs, int njobs, const Job &s
     l.rec_off = 32ull + 4ull * job.nchunks + resolve_pos(l.pos);
 }
 
+// Largest valid record of a chunk of m values: header, flags, and w = W rows of at most
+// cols/64 + cols/8 bytes (a sparse row with no zero byte).
 __device__ __forceinline__ uint32_t max_record(uint32_t m, uint32_t dtype) {
     const uint32_t W = dtype == 0 ? 64u : 32u;
-    return 3u + W / 8u + W / 8u + W * (chunk_cols(m) / 8u);
+    return 3u + W / 8u + W / 8u + W * (chunk_cols(m) / 8u + chunk_cols(m) / 64u);
 }
 
 // Starts the cp.async of a record into rbuf; returns false if its location is invalid.

@@ -32,7 +32,12 @@ struct Job {
     unsigned long long *result;    // [0] stream bytes (compress) / values (decompress), [1] status
     uint32_t block;
     uint32_t dtype;                // 0 = FP64, 1 = FP32
+    uint32_t variant;              // compression: kVariant* (decompression: unused)
 };
+
+// Codec variants: Falcon, and the three ablations of Sec. 5.4.2 (every row sparse, every
+// row dense, Elf's trial-and-error decimal place).  All write the same record layout.
+enum : uint32_t { kVariantFalcon = 0, kVariantSparse = 1, kVariantDense = 2, kVariantElf = 3 };
 
 // Per-launch control block at the start of the workspace (zeroed before each launch); the
 // kernels of this version take their chunks in a fixed stride and do not use its fields.

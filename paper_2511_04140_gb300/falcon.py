@@ -23,6 +23,8 @@ MAX_BLOCK = 1025
 _lock = threading.Lock()
 _lib = None
 COMPRESS, DECOMPRESS = 0, 1
+# codec variants (falcon_variant): Falcon and the ablations of Sec. 5.4.2
+VARIANT_FALCON, VARIANT_SPARSE, VARIANT_DENSE, VARIANT_ELF = 0, 1, 2, 3
 
 
 class Series(ctypes.Structure):
@@ -78,6 +80,10 @@ def _load():
             L.falcon_workspace_bytes.argtypes = [u64]
             L.falcon_compress_async.restype = ci
             L.falcon_compress_async.argtypes = [vp, u64, ci, u32, vp, sz, vp, sz, vp, vp]
+            L.falcon_compress_variant_async.restype = ci
+            L.falcon_compress_variant_async.argtypes = [vp, u64, ci, u32, ci, vp, sz, vp, sz, vp, vp]
+            L.falcon_variant_bound.restype = sz
+            L.falcon_variant_bound.argtypes = [u64, ci, u32, ci]
             L.falcon_decompress_async.restype = ci
             L.falcon_decompress_async.argtypes = [vp, sz, vp, vp, sz, vp, sz, vp, vp]
             L.falcon_release.restype = ci
@@ -140,6 +146,10 @@ def bound(n: int, dtype_code: int, block: int = 1024) -> int:
     return _load().falcon_bound(n, dtype_code, block)
 
 
+def variant_bound(n: int, dtype_code: int, block: int, variant: int) -> int:
+    return _load().falcon_variant_bound(n, dtype_code, block, variant)
+
+
 def workspace_bytes(nchunks: int) -> int:
     return _load().falcon_workspace_bytes(nchunks)
 
@@ -193,6 +203,30 @@ def compress_async(x: torch.Tensor, block: int, out: torch.Tensor, workspace: to
     _check(_load().falcon_compress_async(x.data_ptr(), x.numel(), _dtype_code(x), block, out.data_ptr(),
                                          out.numel(), workspace.data_ptr(), workspace.numel(),
                                          result.data_ptr(), _stream_ptr(stream)), "compress_async")
+
+
+def compress_variant_async(x: torch.Tensor, block: int, variant: int, out: torch.Tensor, workspace: torch.Tensor,
+                           result: torch.Tensor, stream=None) -> None:
+    """compress_async for a codec variant (VARIANT_*); size `out` with variant_bound."""
+    _check(_load().falcon_compress_variant_async(x.data_ptr(), x.numel(), _dtype_code(x), block, variant,
+                                                 out.data_ptr(), out.numel(), workspace.data_ptr(),
+                                                 workspace.numel(), result.data_ptr(), _stream_ptr(stream)),
+           "compress_variant_async")
+
+
+def compress_variant(x: torch.Tensor, block: int, variant: int, stream=None) -> torch.Tensor:
+    """Compresses x with a codec variant (allocates the output and a workspace, synchronises);
+    returns the stream as a uint8 CUDA tensor."""
+    code = _dtype_code(x)
+    out = torch.empty(max(variant_bound(x.numel(), code, block, variant), 32), dtype=torch.uint8, device=x.device)
+    ws = torch.empty(workspace_bytes((x.numel() + block - 1) // block), dtype=torch.uint8, device=x.device)
+    res = torch.zeros(2, dtype=torch.int64, device=x.device)
+    compress_variant_async(x, block, variant, out, ws, res, stream)
+    (stream or torch.cuda.current_stream()).synchronize()
+    nbytes, status = (int(v) for v in res.cpu())
+    if status != OK:
+        raise FalconError(status, "compress_variant")
+    return out[:nbytes]
 
 
 def decompress_async(s: torch.Tensor, nbytes: int, header: bytes, out: torch.Tensor, workspace: torch.Tensor,
