@@ -91,12 +91,19 @@ __device__ __forceinline__ void smem_move_down(uint8_t *buf, uint32_t dst, uint3
     __syncwarp();
 }
 
+// non-zero nibble of x (bit 3 - i set iff byte i is non-zero): the bytes' high-bit flags
+// gathered into the top byte by one multiply
+__device__ __forceinline__ uint32_t nz_nibble(uint32_t x) {
+    const uint32_t y = (((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+    return ((y >> 7) * 0x08040201u) >> 24 & 0xFu;
+}
+
 // Sparse row (Sec. 3.3) written with byte stores at byte offset P of the warp buffer:
 // a bitmap of nact/2 bytes (bit 7 of byte 0 = row byte 0), then the non-zero row bytes.
 // Returns the row's length.
 __device__ __forceinline__ uint32_t sparse_row(uint8_t *buf, uint32_t P, uint32_t x, int lane, uint32_t nact) {
     const bool active = (uint32_t)lane < nact;
-    const uint32_t nib = active ? nonzero_nibble(x) : 0u;
+    const uint32_t nib = active ? nz_nibble(x) : 0u;
     const uint32_t nib_next = __shfl_down_sync(kFull, nib, 1);
     if (active && !(lane & 1)) buf[P + (lane >> 1)] = (uint8_t)((nib << 4) | nib_next);
     const uint32_t cnt = __popc(nib);
@@ -125,62 +132,84 @@ __device__ __forceinline__ typename Traits<F64>::U lane_value(const uint8_t *buf
     return *reinterpret_cast<const U *>(buf + (lane * UN + ((k / PER) ^ (lane & 7))) * 16 + (k % PER) * Traits<F64>::S);
 }
 
-// Every value of the chunk passes Alg. 2's test at a.  The values are re-read from the
-// staging buffer; this runs a few times per Case-1 chunk only.
+// Every value of the chunk (the lane's 32 in v, value 1024 of a 1025-value chunk in vx)
+// passes Alg. 2's test at a.  Values past m are +0, which passes.
+// A failing decimal place usually fails on every lane's first value already, so those 32
+// are tested first.
 template <bool F64>
-__device__ __noinline__ bool all_pass(const uint8_t *buf, int lane, uint32_t m, typename Traits<F64>::U vx, int a) {
+__device__ __forceinline__ bool all_pass(const typename Traits<F64>::U (&v)[32], typename Traits<F64>::U vx, int a) {
+    if (!__all_sync(kFull, q_test(v[0], a))) return false;
     bool ok = q_test(vx, a);
-#pragma unroll 4
-    for (int k = 0; k < 32; ++k) {
-        if (32u * lane + k < m) ok &= q_test(lane_value<F64>(buf, lane, k), a);
-    }
+#pragma unroll
+    for (int k = 1; k < 32; ++k) ok &= q_test(v[k], a);
     return __all_sync(kFull, ok);
 }
 
 // FP64: smallest a in [0, atop] at which every value passes, or -1 (Case 2).  For chunks of
 // valid values the predicate is monotone in a (Thm 4 with Thm 3); a single failure at atop
-// means some value is an exception or needs alpha > atop.
-__device__ int search_alpha64(const uint8_t *buf, int lane, uint32_t m, uint64_t vx, int atop, int hint) {
-    int lo, hi;
-    if (hint >= 0 && hint < atop) {
-        if (all_pass<true>(buf, lane, m, vx, hint)) {
-            if (hint == 0 || !all_pass<true>(buf, lane, m, vx, hint - 1)) return hint;
-            lo = 0;
-            hi = hint - 1;
+// means some value is an exception or needs alpha > atop.  The first probe is the previous
+// chunk's alpha (hint), the second the one below it, then bisection; one call site keeps
+// the inlined test once in the code.
+__device__ __forceinline__ int search_alpha64(const uint64_t (&v)[32], uint64_t vx, int atop, int hint) {
+    int lo = 0, hi = atop;                      // the answer, if any, lies in [lo, hi]
+    bool hi_ok = false;                         // all_pass(hi) is known to hold
+    int a = (hint >= 0 && hint < atop) ? hint : atop;
+    bool first_ok = false, probed_below = false;
+#pragma unroll 1
+    for (;;) {
+        const bool ok = all_pass<true>(v, vx, a);
+        if (ok) {
+            hi = a;
+            hi_ok = true;
         } else {
-            if (!all_pass<true>(buf, lane, m, vx, atop)) return -1;
-            lo = hint + 1;
-            hi = atop;
+            if (a == atop) return -1;
+            lo = a + 1;
         }
-    } else {
-        if (!all_pass<true>(buf, lane, m, vx, atop)) return -1;
-        lo = 0;
-        hi = atop;
+        if (hi_ok && lo >= hi) return hi;
+        if (!hi_ok) {
+            a = atop;                           // the hint failed: is Case 1 possible at all?
+        } else if (ok && !probed_below && !first_ok) {
+            first_ok = true;
+            probed_below = true;
+            a = hi - 1;                         // most chunks keep their neighbour's alpha
+        } else {
+            a = (lo + hi) >> 1;                 // lo <= a < hi
+        }
+        first_ok = true;
     }
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (all_pass<true>(buf, lane, m, vx, mid)) hi = mid;
-        else lo = mid + 1;
-    }
-    return hi;
 }
 
-// FP32: alpha_max = max over values of Alg. 2's decimal place (first_pass_f32), then the R6
-// check that every value round-trips at alpha_max; -1 means Case 2.
-__device__ int alpha32(const uint8_t *buf, int lane, uint32_t m, uint32_t vx, int atop) {
-    int amax = first_pass_f32(vx, atop);
-    bool bad = amax < 0;
-#pragma unroll 4
-    for (int k = 0; k < 32; ++k) {
-        if (32u * lane + k < m) {
-            const int a = first_pass_f32(lane_value<false>(buf, lane, k), atop);
-            bad |= a < 0;
-            amax = a > amax ? a : amax;
+// FP32: alpha_max = max over values of Alg. 2's decimal place (the first a with eps <= mu,
+// accepted only if the round trip holds there), restricted to [0, atop], then the R6 check
+// that every value round-trips at alpha_max; -1 means Case 2.  The values are tested a
+// decimal place at a time, all 32 of a lane together (no divergent per-value loops).
+__device__ __forceinline__ int alpha32(const uint32_t (&v)[32], uint32_t vx, bool has_vx, int atop) {
+    uint32_t open = 0xFFFFFFFFu;                // values of this lane still without a decimal place
+    bool open_x = has_vx;
+    bool bad = false;
+    int amax = 0;
+#pragma unroll 1
+    for (int a = 0; a <= atop; ++a) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            bool rt;
+            if (alg2_step_f32(v[k], a, rt) && ((open >> k) & 1u)) {
+                open &= ~(1u << k);
+                bad |= !rt;
+                amax = a;
+            }
         }
+        bool rt;
+        if (alg2_step_f32(vx, a, rt) && open_x) {
+            open_x = false;
+            bad |= !rt;
+            amax = a;
+        }
+        if (!__any_sync(kFull, open != 0u || open_x)) break;
     }
-    if (__any_sync(kFull, bad)) return -1;
+    if (__any_sync(kFull, bad || open != 0u || open_x)) return -1;
     amax = (int)__reduce_max_sync(kFull, (uint32_t)amax);
-    return all_pass<false>(buf, lane, m, vx, amax) ? amax : -1;
+    return all_pass<false>(v, vx, amax) ? amax : -1;
 }
 
 // Fal._Elf's decimal place of one value (Sec. 1's trial and error, ablation of Sec. 5.4.2):
@@ -214,22 +243,20 @@ __device__ __forceinline__ int elf_dp(uint32_t u) {
 // Fal._Elf: alpha_max = the largest of the values' Elf decimal places, then Eq. 4's bounds and
 // the R6 round trip at alpha_max, as for Falcon; -1 means Case 2.
 template <bool F64>
-__device__ int alpha_elf(const uint8_t *buf, int lane, uint32_t m, typename Traits<F64>::U vx, int e_max) {
+__device__ int alpha_elf(const typename Traits<F64>::U (&v)[32], typename Traits<F64>::U vx, bool has_vx, int e_max) {
     using T = Traits<F64>;
-    int amax = (m > 1024u && lane == 31) ? elf_dp(vx) : 0;
+    int amax = has_vx ? elf_dp(vx) : 0;
     bool bad = amax < 0;
-#pragma unroll 1
-    for (int k = 0; k < 32; ++k) {
-        if (32u * lane + k < m) {
-            const int a = elf_dp(lane_value<F64>(buf, lane, k));
-            bad |= a < 0;
-            amax = a > amax ? a : amax;
-        }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {              // values past m are +0: decimal place 0
+        const int a = elf_dp(v[k]);
+        bad |= a < 0;
+        amax = a > amax ? a : amax;
     }
     if (__any_sync(kFull, bad)) return -1;
     amax = (int)__reduce_max_sync(kFull, (uint32_t)amax);
     if (amax > T::A_MAX || amax + e_max + 1 > T::B_MAX) return -1;
-    return all_pass<F64>(buf, lane, m, vx, amax) ? amax : -1;
+    return all_pass<F64>(v, vx, amax) ? amax : -1;
 }
 
 __device__ __forceinline__ void issue_chunk(const Job *jobs, int njobs, const Job &single, uint64_t t,
@@ -253,11 +280,11 @@ __device__ __forceinline__ unsigned long long pack_meta(int alpha_byte, int beta
 }
 
 // G (Eq. 4) and Z (Eq. 5) in place: v[k] becomes Z of column 32 lane + k, pad columns (R11)
-// are zero; alpha < 0 means Case 2.  Returns z_1 (every lane) and the OR of the lane's Z.
+// are zero; alpha < 0 means Case 2.  Returns z_1 (every lane).
 template <bool F64>
 __device__ __forceinline__ typename Traits<F64>::U to_z(typename Traits<F64>::U (&v)[32],
                                                         typename Traits<F64>::U vx, int alpha, uint32_t m,
-                                                        int lane, typename Traits<F64>::U &zor) {
+                                                        int lane) {
     using U = typename Traits<F64>::U;
     U gx;
     if (alpha >= 0) {
@@ -272,20 +299,20 @@ __device__ __forceinline__ typename Traits<F64>::U to_z(typename Traits<F64>::U 
     const U z1 = shfl_x(v[0], 0);
     U nxt = shfl_down_x(v[0], 1);
     if (lane == 31) nxt = gx;
-    zor = 0;
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
         const U hi = (k < 31) ? v[k + 1] : nxt;
         v[k] = zigzag((U)(hi - v[k]));          // v now holds Z of columns 32*lane + k
-        zor |= v[k];
     }
-    if (32u * lane + 32u >= m) {                 // pad columns (R11): only the last lanes
-        zor = 0;
+    // pad columns (R11): column c holds z_{c+2}, a pad when c + 1 >= m.  A full chunk of 1024
+    // values has one (the last column of lane 31), 1025 values none; only tail chunks take the
+    // general loop.
+    if (m == 1024u) {
+        if (lane == 31) v[31] = 0;
+    } else if (m < 1024u && 32u * lane + 32u >= m) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
+        for (int k = 0; k < 32; ++k)
             if (32u * lane + k + 1u >= m) v[k] = 0;
-            zor |= v[k];
-        }
     }
     return z1;
 }
@@ -360,7 +387,7 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
             const int e_max = floor_log10(vmax);
             const int atop = min(T::A_MAX, T::B_MAX - 1 - e_max);
             if (job.variant == kVariantElf) {
-                alpha = alpha_elf<F64>(buf, lane, m, vx, e_max);
+                alpha = alpha_elf<F64>(v, vx, m > 1024u && lane == 31, e_max);
             } else if (atop >= 0) {
                 // quick rejection: Alg. 2 on the largest magnitude first.  The test reads
                 // only |v|, so it runs on vmax itself, the same in every lane.
@@ -368,8 +395,8 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
                 if constexpr (F64) fail = !q_test(vmax, atop);
                 else fail = first_pass_f32(vmax, atop) < 0;
                 if (!fail) {
-                    if constexpr (F64) alpha = search_alpha64(buf, lane, m, vx, atop, hint);
-                    else alpha = alpha32(buf, lane, m, vx, atop);
+                    if constexpr (F64) alpha = search_alpha64(v, vx, atop, hint);
+                    else alpha = alpha32(v, vx, m > 1024u && lane == 31, atop);
                 }
             }
             if (alpha >= 0) beta_hat = alpha + e_max + 1;
@@ -380,8 +407,7 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
     next();                                     // the staged values have been read
 
     // ---- 3. G, Z, w (from the ORs of 8-column groups that step 4 uses) -------------------------
-    U zor;
-    (void)to_z<F64>(v, vx, alpha, m, lane, zor);
+    (void)to_z<F64>(v, vx, alpha, m, lane);
     U o[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -390,7 +416,7 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
         for (int j = 1; j < 8; ++j) x |= v[8 * i + j];
         o[i] = x;
     }
-    zor = warp_or_x((U)(o[0] | o[1] | o[2] | o[3]));
+    const U zor = warp_or_x((U)(o[0] | o[1] | o[2] | o[3]));
     const int w = zor ? (T::W - (F64 ? __clzll((long long)zor) : __clz((int)zor))) : 0;
 
     // ---- 4. non-zero bytes per row, without forming the bit planes ----------------------------
@@ -519,8 +545,7 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     load_own<F64>(src, lane, m, v);
     U vx = 0;                                   // value 1024 of a 1025-value chunk
     if (m > 1024u && lane == 31) vx = __ldg(reinterpret_cast<const U *>(src) + 1024);
-    U zor;
-    const U z1 = to_z<F64>(v, vx, alpha, m, lane, zor);
+    const U z1 = to_z<F64>(v, vx, alpha, m, lane);
     if (lane == 0) bulk_wait_read();             // the previous record has left the buffer
     __syncwarp();
     // half h of the values holds planes 32 h .. 32 h + 31 (the high half only when w > 32)
@@ -551,15 +576,14 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     // Row r (plane w-r) ends before byte 37 + 128 r of the buffer (37 + 144 r when every row
     // is sparse, wide layout) while the plane read next starts at kPlOff + (64 - w + r) * 128
     // >= kPlOff + 128 r: nothing unread is overwritten.
-    if ((uint32_t)lane < hdr) {
-        uint32_t byte;
+    {
+        // header byte `lane` (branch-free: every lane computes its byte, lanes < hdr store it)
         const int i = lane;
-        if (i == 0) byte = (uint32_t)pd.alpha_byte;
-        else if (i == 1) byte = (uint32_t)pd.beta_hat;
-        else if (i < 2 + T::Z1B) byte = (uint32_t)(pd.z1 >> (8 * (i - 2))) & 0xFFu;
-        else if (i == 2 + T::Z1B) byte = (uint32_t)w;
-        else byte = (uint32_t)(dense_mask >> (8u * (flag_bytes - 1u - (uint32_t)(i - 3 - T::Z1B)))) & 0xFFu;
-        buf[sh + i] = (uint8_t)byte;
+        const uint32_t zb = (uint32_t)(pd.z1 >> ((8 * (i - 2)) & 63)) & 0xFFu;
+        const uint32_t fb = (uint32_t)(dense_mask >> ((8u * (flag_bytes - 1u - (uint32_t)(i - 3 - T::Z1B))) & 63u)) & 0xFFu;
+        uint32_t byte = i < 2 + T::Z1B ? zb : ((i == 2 + T::Z1B) ? (uint32_t)w : fb);
+        byte = i == 0 ? (uint32_t)pd.alpha_byte : (i == 1 ? (uint32_t)pd.beta_hat : byte);
+        if ((uint32_t)lane < hdr) buf[sh + i] = (uint8_t)byte;
     }
     __syncwarp();
     uint32_t pos = sh + hdr;                      // next record byte in the buffer

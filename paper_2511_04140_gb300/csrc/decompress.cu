@@ -45,6 +45,8 @@ __device__ __forceinline__ void init_expand_sel() {
     }
 }        // one record buffer, one plane buffer
 
+// fl(fl(g) / 10^a) with IEEE FP64 operations, as the decoder defines it for any g; the hot
+// path takes div_pow10_exact for |g| < 2^53 (every g an encoder writes: |g| < 10^15).
 __device__ __forceinline__ double div_pow10(int64_t g, int a) {
     return __ddiv_rn(__ll2double_rn(g), __longlong_as_double((long long)FALCON_P10_F64[a - FALCON_P10_F64_LO]));
 }
@@ -182,17 +184,19 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     const uint32_t hdr = pos;
     const uint64_t wmask = (w >= 64u) ? ~0ull : ((1ull << w) - 1ull);
     // Sparse rows only (top to bottom): a sparse row's position is the header, the dense rows
-    // above it (row_bytes each) and the sparse rows above it.  Dense rows need no walk.
+    // above it (row_bytes each) and the sparse rows above it.  Dense rows need no walk.  No
+    // position is checked here: a row takes at most 16 + 128 bytes, so every read stays in the
+    // record buffer whatever the bytes say, and the size check after the walk (every row's
+    // bytes add up to the record size) rejects a malformed record before anything is stored.
     uint64_t sparse = bad ? 0ull : (~dense_mask & wmask);
     uint32_t sparse_sum = 0, walked = 0;       // sparse rows above the current one
 #pragma unroll 1
-    while (sparse && !bad) {
+    while (sparse) {
         const int p = 63 - __clzll((long long)sparse);
         sparse &= ~(1ull << p);
         // rows above p: w - 1 - p, of which `walked` are sparse
         const uint32_t spos = hdr + row_bytes * (w - 1u - (uint32_t)p - walked) + sparse_sum;
         ++walked;
-        if (spos + bm_bytes > size) { bad = true; break; }
         uint32_t nib = 0;
         if (active) {
             const uint32_t byte = rec[spos + (lane >> 1)];
@@ -205,10 +209,9 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
         const unsigned lt = (1u << lane) - 1u;
         const uint32_t before = __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt);
         const uint32_t nnz = __reduce_add_sync(kFull, cnt);
-        if (spos + bm_bytes + nnz > size) { bad = true; break; }
         // the lane's non-zero bytes start at record byte spos + bm_bytes + before: load the
-        // four bytes from there (two aligned words, at most 7 bytes past the record, inside
-        // the buffer) and put each in its place with one byte permute
+        // four bytes from there (two aligned words) and put each in its place with one byte
+        // permute (selector by the bitmap nibble)
         const uint32_t qa = sh + spos + bm_bytes + before;
         const uint32_t *wq = reinterpret_cast<const uint32_t *>(rbuf + (qa & ~3u));
         const uint32_t word = __funnelshift_r(wq[0], wq[1], (qa & 3u) * 8u);
@@ -247,9 +250,12 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     }
     __syncwarp();
     next();                                       // the record has been read
+    // Slots of planes >= w hold stale bytes: they are masked off after each transpose (bit p
+    // of every value), one AND per value instead of a select per word.  Lanes >= nact (tail
+    // chunks) gather stale words too; their columns lie past the chunk's values and are never
+    // stored, and they only feed the scan of later lanes.
     auto plane_word = [&](int p) -> uint32_t {
-        const uint32_t x = *reinterpret_cast<const uint32_t *>(pbuf + (63 - p) * 128 + 4 * lane);
-        return ((uint32_t)p < w && active) ? x : 0u;
+        return *reinterpret_cast<const uint32_t *>(pbuf + (63 - p) * 128 + 4 * lane);
     };
     U d[32];
     if constexpr (F64) {
@@ -258,8 +264,9 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
 #pragma unroll
             for (int i = 0; i < 32; ++i) a[i] = plane_word(i + 32);
             transpose32(a);
+            const uint32_t keep = w >= 64 ? ~0u : ((1u << (w - 32)) - 1u);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) d[k] = (U)a[k ^ 7] << 32;
+            for (int k = 0; k < 32; ++k) d[k] = (U)(a[k ^ 7] & keep) << 32;
         } else {
 #pragma unroll
             for (int k = 0; k < 32; ++k) d[k] = 0;
@@ -270,12 +277,13 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
 #pragma unroll
         for (int p = 0; p < 32; ++p) a[p] = plane_word(p);
         transpose32(a);
+        const uint32_t keep = w >= 32 ? ~0u : ((1u << w) - 1u);
         if constexpr (F64) {
 #pragma unroll
-            for (int k = 0; k < 32; ++k) d[k] |= (U)a[k ^ 7];
+            for (int k = 0; k < 32; ++k) d[k] |= (U)(a[k ^ 7] & keep);
         } else {
 #pragma unroll
-            for (int k = 0; k < 32; ++k) d[k] = (U)a[k ^ 7];
+            for (int k = 0; k < 32; ++k) d[k] = (U)(a[k ^ 7] & keep);
         }
     }
     U run = 0;
@@ -287,11 +295,25 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     const U gbase = z1 + lane_off;               // G of value 32*lane + k + 1 = gbase + d[k]
     const bool case1 = alpha <= (uint32_t)T::A_MAX && beta_hat <= (uint32_t)T::B_MAX;
     if (case1) {
+        if constexpr (F64) {
+            // |g| >= 2^53 only in streams no encoder writes: then every value takes the FP64 path
+            bool big = false;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const U gk = gbase + d[k];
-            if constexpr (F64) d[k] = (U)__double_as_longlong(div_pow10((int64_t)gk, (int)alpha));
-            else d[k] = (U)__float_as_uint(div_pow10((int32_t)gk, (int)alpha));
+            for (int k = 0; k < 32; ++k) {
+                const uint64_t gk = gbase + d[k];
+                big |= (gk + (1ull << 53)) > (1ull << 54);          // |g| > 2^53
+            }
+            if (__any_sync(kFull, big)) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    d[k] = (U)__double_as_longlong(div_pow10((int64_t)(gbase + d[k]), (int)alpha));
+            } else {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) d[k] = div_pow10_exact((int64_t)(gbase + d[k]), (int)alpha);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) d[k] = (U)__float_as_uint(div_pow10((int32_t)(gbase + d[k]), (int)alpha));
         }
     } else {
 #pragma unroll
@@ -299,8 +321,13 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     }
     U v0;
     if (case1) {
-        if constexpr (F64) v0 = (U)__double_as_longlong(div_pow10((int64_t)z1, (int)alpha));
-        else v0 = (U)__float_as_uint(div_pow10((int32_t)z1, (int)alpha));
+        if constexpr (F64) {
+            const uint64_t g1 = z1;
+            v0 = ((g1 + (1ull << 53)) > (1ull << 54)) ? (U)__double_as_longlong(div_pow10((int64_t)g1, (int)alpha))
+                                                       : div_pow10_exact((int64_t)g1, (int)alpha);
+        } else {
+            v0 = (U)__float_as_uint(div_pow10((int32_t)z1, (int)alpha));
+        }
     } else {
         v0 = unzigzag(z1);
     }

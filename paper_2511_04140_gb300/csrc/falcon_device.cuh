@@ -313,6 +313,14 @@ __device__ __forceinline__ bool q_test(uint64_t u, int a) {
     if (F <= 0) return true;
     if (F >= 128) return false;
     const uint64_t p5 = FALCON_POW5[a];
+    if (F <= 64) {
+        // the low F bits of P are the low bits of the 64-bit product: no 128-bit arithmetic
+        const uint64_t mask = (F == 64) ? ~0ull : ((1ull << F) - 1ull);
+        const uint64_t r = (m * p5) & mask;
+        const uint64_t lim = p5 >> 1;
+        if (r > (mask >> 1)) return (mask - r) + 1ull <= lim;          // r >= 2^(F-1)
+        return r <= ((m == 0x0010000000000000ull) ? ((p5 - 1) >> 2) : lim);
+    }
     const unsigned __int128 P = (unsigned __int128)m * p5;
     const unsigned __int128 one = 1;
     const unsigned __int128 r = P & ((one << F) - 1);
@@ -321,21 +329,11 @@ __device__ __forceinline__ bool q_test(uint64_t u, int a) {
     if (r >= half) return ((one << F) - r) <= lim;
     return r <= ((m == 0x0010000000000000ull) ? ((p5 - 1) >> 2) : lim);
 }
+__device__ __forceinline__ bool alg2_step_f32(uint32_t u, int a, bool &rt);
 __device__ __forceinline__ bool q_test(uint32_t u, int a) {
-    const uint32_t au = u & 0x7FFFFFFFu;
-    if (au == 0) return true;
-    const int E = (int)(au >> 23) - 150;
-    const uint64_t m = (au & 0x007FFFFFu) | 0x00800000u;
-    const int F = -(E + a);
-    if (F <= 0) return true;
-    if (F >= 64) return false;
-    const uint64_t p5 = FALCON_POW5[a];
-    const uint64_t P = m * p5;
-    const uint64_t r = P & ((1ull << F) - 1);
-    const uint64_t half = 1ull << (F - 1);
-    const uint64_t lim = p5 >> 1;
-    if (r >= half) return ((1ull << F) - r) <= lim;
-    return r <= ((m == 0x00800000u) ? ((p5 - 1) >> 2) : lim);
+    bool rt;
+    (void)alg2_step_f32(u, a, rt);
+    return rt;
 }
 
 // Alg. 2's first test alone (eps <= mu) for FP32, on the exact product x = v * 10^a (R14):
@@ -355,6 +353,31 @@ __device__ __forceinline__ bool eps_le_mu(uint32_t u, int a) {
     return dist <= (P >> 23);
 }
 
+// Both tests of Alg. 2 for FP32 at decimal place a, from one product: eps <= mu (returned)
+// and the round trip (rt), as eps_le_mu and q_test compute them.  P = m 5^a < 2^48 comes from
+// one 32 x 32 -> 64 multiply; for F < 32 the remainder and both bounds are 32-bit.
+__device__ __forceinline__ bool alg2_step_f32(uint32_t u, int a, bool &rt) {
+    const uint32_t au = u & 0x7FFFFFFFu;
+    const int F = 150 - (int)(au >> 23) - a;
+    if (au == 0 || F <= 0) { rt = true; return true; }
+    if (F >= 64) { rt = false; return false; }
+    const uint32_t m = (au & 0x007FFFFFu) | 0x00800000u;
+    const uint32_t p5 = (uint32_t)FALCON_POW5[a];          // 5^a < 2^24 for a <= 10
+    const uint64_t P = (uint64_t)m * p5;
+    const uint32_t lim = p5 >> 1, lim_low = (m == 0x00800000u) ? ((p5 - 1u) >> 2) : lim;
+    const uint32_t mu = (uint32_t)(P >> 23);                // < 2^25
+    if (F < 32) {
+        const uint32_t mask = (1u << F) - 1u;
+        const uint32_t r = (uint32_t)P & mask, rc = mask - r + 1u;
+        rt = (r > (mask >> 1)) ? (rc <= lim) : (r <= lim_low);
+        return (r < rc ? r : rc) <= mu;
+    }
+    const uint64_t mask = (1ull << F) - 1ull;
+    const uint64_t r = P & mask, rc = mask - r + 1ull;
+    rt = (r > (mask >> 1)) ? (rc <= lim) : (r <= lim_low);
+    return (r < rc ? r : rc) <= mu;
+}
+
 // FP32 decimal place of one value as Alg. 2 finds it, restricted to [0, atop]: the first a
 // with eps <= mu, accepted only if the round trip holds there; -1 otherwise (an exception
 // or a decimal place beyond atop, both of which make the chunk Case 2).  The 24-bit
@@ -367,18 +390,19 @@ __device__ __forceinline__ int first_pass_f32(uint32_t u, int atop) {
     return -1;
 }
 
-// g = round(v (x) 10^a) (Eq. 4, Case 1) for a value that passed q_test at a.
+// g = round(v (x) 10^a) (Eq. 4, Case 1) for a value that passed q_test at a.  Passing means
+// X = v 10^a lies within 5^a / 2^(F+1) <= 1/8 of the integer g (the rounding interval of v,
+// scaled), so an approximation of X closer than 3/8 rounds to g: with m and 5^a both
+// normalised to 64 bits, mulhi(m 2^11, 5^a 2^(63-d)) = floor(X 2^sh), sh = F + 10 - d >= 13,
+// is X within 2^-13, and rounding it at bit sh gives g.  One 64-bit high product per value.
 __device__ __forceinline__ uint64_t case1_g(uint64_t u, int a) {
     const uint64_t au = u & 0x7FFFFFFFFFFFFFFFull;
     if (au == 0) return 0;
     const int E = (int)(au >> 52) - 1075;
     const uint64_t m = (au & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
-    const int F = -(E + a);
-    const uint64_t p5 = FALCON_POW5[a];
-    const unsigned __int128 P = (unsigned __int128)m * p5;
-    uint64_t N;
-    if (F <= 0) N = (uint64_t)(P << (-F));
-    else N = (uint64_t)((P + ((unsigned __int128)1 << (F - 1))) >> F);
+    const int sh = -(E + a) + 10 - (int)FALCON_LOG2_POW5[a];
+    const uint64_t t = __umul64hi(m << 11, FALCON_POW5_NORM[a]);
+    const uint64_t N = ((t >> (sh - 1)) + 1ull) >> 1;
     return (u >> 63) ? (0ull - N) : N;
 }
 __device__ __forceinline__ uint32_t case1_g(uint32_t u, int a) {
@@ -392,6 +416,41 @@ __device__ __forceinline__ uint32_t case1_g(uint32_t u, int a) {
     if (F <= 0) N = P << (-F);
     else N = (P + (1ull << (F - 1))) >> F;
     return (u >> 31) ? (0u - (uint32_t)N) : (uint32_t)N;
+}
+
+// fl(g / 10^a), correctly rounded (nearest, ties to even), for |g| < 2^53 and 0 <= a <= 22, in
+// integer arithmetic (the inverse of Eq. 4, Case 1).  g / 10^a = (g / 5^a) 2^-a and the
+// scaling by 2^-a is exact (no result is subnormal), so the work is one correctly rounded
+// division by 5^a: with G = |g| normalised to [2^63, 2^64), d = floor(log2 5^a) and the
+// reciprocal R = floor(2^(64+d) / 5^a), T = mulhi(G, R) is floor(G 2^d / 5^a) or one less
+// (division by an invariant integer, Granlund and Montgomery, PLDI 1994); the remainder,
+// below 2 * 5^a, is exact in 64-bit arithmetic and corrects T.  T has 63 or 64 significant
+// bits; its top 53 bits, the next bit and a sticky bit (lower bits or a non-zero remainder)
+// round to the IEEE significand.  Returns the bits of the double.
+__device__ __forceinline__ uint64_t div_pow10_exact(int64_t g, int a) {
+    if (g == 0) return 0;
+    const uint64_t sign = (uint64_t)g & 0x8000000000000000ull;
+    const uint64_t ag = g < 0 ? 0ull - (uint64_t)g : (uint64_t)g;
+    const int s = __clzll((long long)ag);
+    const uint64_t G = ag << s;
+    uint64_t T = G, r = 0;
+    int d = 0;
+    if (a > 0) {
+        d = FALCON_LOG2_POW5[a];
+        const uint64_t D = FALCON_POW5[a];
+        T = __umul64hi(G, FALCON_RECIP5[a]);
+        r = (G << d) - T * D;                   // true remainder in [0, 2 D): exact mod 2^64
+        if (r >= D) { r -= D; ++T; }
+    }
+    const int lz = __clzll((long long)T);       // 0 or 1
+    const uint64_t Tn = T << lz;
+    uint64_t mant = Tn >> 11;
+    const uint32_t rest = (uint32_t)Tn & 0x7FFu;
+    const bool sticky = (rest & 0x3FFu) != 0u || r != 0;
+    if ((rest & 0x400u) && (sticky || (mant & 1ull))) ++mant;
+    int e2 = 11 - lz - d - s - a;               // the value is mant * 2^e2
+    if (mant == (1ull << 53)) { mant >>= 1; ++e2; }
+    return sign | ((uint64_t)(e2 + 52 + 1023) << 52) | (mant & 0x000FFFFFFFFFFFFFull);
 }
 
 __device__ __forceinline__ void set_status(unsigned long long *result, uint32_t code) {

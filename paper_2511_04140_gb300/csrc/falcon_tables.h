@@ -37,6 +37,62 @@ FALCON_TABLE_QUAL uint64_t FALCON_POW5[23] = {
     0x000878678326eac9ull, /* 5^22 */
 };
 
+FALCON_TABLE_QUAL uint64_t FALCON_RECIP5[23] = {
+    0x0000000000000000ull, /* 5^0 */
+    0xccccccccccccccccull, /* 5^1 */
+    0xa3d70a3d70a3d70aull, /* 5^2 */
+    0x83126e978d4fdf3bull, /* 5^3 */
+    0xd1b71758e219652bull, /* 5^4 */
+    0xa7c5ac471b478423ull, /* 5^5 */
+    0x8637bd05af6c69b5ull, /* 5^6 */
+    0xd6bf94d5e57a42bcull, /* 5^7 */
+    0xabcc77118461cefcull, /* 5^8 */
+    0x89705f4136b4a597ull, /* 5^9 */
+    0xdbe6fecebdedd5beull, /* 5^10 */
+    0xafebff0bcb24aafeull, /* 5^11 */
+    0x8cbccc096f5088cbull, /* 5^12 */
+    0xe12e13424bb40e13ull, /* 5^13 */
+    0xb424dc35095cd80full, /* 5^14 */
+    0x901d7cf73ab0acd9ull, /* 5^15 */
+    0xe69594bec44de15bull, /* 5^16 */
+    0xb877aa3236a4b449ull, /* 5^17 */
+    0x9392ee8e921d5d07ull, /* 5^18 */
+    0xec1e4a7db69561a5ull, /* 5^19 */
+    0xbce5086492111aeaull, /* 5^20 */
+    0x971da05074da7beeull, /* 5^21 */
+    0xf1c90080baf72cb1ull, /* 5^22 */
+};
+
+FALCON_TABLE_QUAL uint64_t FALCON_POW5_NORM[23] = {
+    0x8000000000000000ull, /* 5^0 */
+    0xa000000000000000ull, /* 5^1 */
+    0xc800000000000000ull, /* 5^2 */
+    0xfa00000000000000ull, /* 5^3 */
+    0x9c40000000000000ull, /* 5^4 */
+    0xc350000000000000ull, /* 5^5 */
+    0xf424000000000000ull, /* 5^6 */
+    0x9896800000000000ull, /* 5^7 */
+    0xbebc200000000000ull, /* 5^8 */
+    0xee6b280000000000ull, /* 5^9 */
+    0x9502f90000000000ull, /* 5^10 */
+    0xba43b74000000000ull, /* 5^11 */
+    0xe8d4a51000000000ull, /* 5^12 */
+    0x9184e72a00000000ull, /* 5^13 */
+    0xb5e620f480000000ull, /* 5^14 */
+    0xe35fa931a0000000ull, /* 5^15 */
+    0x8e1bc9bf04000000ull, /* 5^16 */
+    0xb1a2bc2ec5000000ull, /* 5^17 */
+    0xde0b6b3a76400000ull, /* 5^18 */
+    0x8ac7230489e80000ull, /* 5^19 */
+    0xad78ebc5ac620000ull, /* 5^20 */
+    0xd8d726b7177a8000ull, /* 5^21 */
+    0x878678326eac9000ull, /* 5^22 */
+};
+
+FALCON_TABLE_QUAL uint8_t FALCON_LOG2_POW5[23] = {
+    0, 2, 4, 6, 9, 11, 13, 16, 18, 20, 23, 25, 27, 30, 32, 34, 37, 39, 41, 44, 46, 48, 51
+};
+
 FALCON_TABLE_QUAL uint64_t FALCON_P10_F64[53] = {
     0x39b4484bfeebc2a0ull, /* fl64(1e-30) */
     0x39e95a5efea6b347ull, /* fl64(1e-29) */

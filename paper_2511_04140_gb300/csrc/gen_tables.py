@@ -2,6 +2,10 @@
 rational arithmetic (Python's Fraction -> float conversion rounds exactly once).
 
   FALCON_POW5[a]          5^a for a = 0..22 (exact integers)
+  FALCON_RECIP5[a]        floor(2^(64 + d) / 5^a) with d = floor(log2 5^a), a = 1..22 (a 64-bit
+                          reciprocal in [2^63, 2^64); entry 0 unused)
+  FALCON_LOG2_POW5[a]     d = floor(log2 5^a)
+  FALCON_POW5_NORM[a]     5^a << (63 - d): 5^a with its top bit at bit 63
   FALCON_P10_F64[k - LO]  bits of fl64(10^k), k in [-30, 22]
   FALCON_P10_F32[k - LO]  bits of fl32(10^k), k in [-15, 10]
 
@@ -40,6 +44,13 @@ def main():
            f"#define FALCON_P10_F32_LO ({F32_LO})", f"#define FALCON_P10_F32_HI ({F32_HI})", "",
            "FALCON_TABLE_QUAL uint64_t FALCON_POW5[23] = {"]
     out += [f"    0x{5 ** a:016x}ull, /* 5^{a} */" for a in range(23)]
+    out += ["};", "", "FALCON_TABLE_QUAL uint64_t FALCON_RECIP5[23] = {"]
+    out += [f"    0x{(0 if a == 0 else (1 << (64 + (5 ** a).bit_length() - 1)) // 5 ** a):016x}ull, /* 5^{a} */"
+            for a in range(23)]
+    out += ["};", "", "FALCON_TABLE_QUAL uint64_t FALCON_POW5_NORM[23] = {"]
+    out += [f"    0x{(5 ** a) << (64 - (5 ** a).bit_length()):016x}ull, /* 5^{a} */" for a in range(23)]
+    out += ["};", "", "FALCON_TABLE_QUAL uint8_t FALCON_LOG2_POW5[23] = {"]
+    out += ["    " + ", ".join(str((5 ** a).bit_length() - 1) for a in range(23))]
     out += ["};", "", f"FALCON_TABLE_QUAL uint64_t FALCON_P10_F64[{F64_HI - F64_LO + 1}] = {{"]
     out += [f"    0x{f64_bits(Fraction(10) ** k):016x}ull, /* fl64(1e{k}) */"
             for k in range(F64_LO, F64_HI + 1)]
