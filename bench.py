@@ -45,7 +45,13 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-pipeline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=1.0, help=argparse.SUPPRESS)
+    ap.add_argument("--no-case1", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-schedulers", action="store_true")
+    ap.add_argument("--no-sweeps", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help=argparse.SUPPRESS)
+    ap.add_argument("--serve-seconds-saturated", type=float, default=3.0, help=argparse.SUPPRESS)
+    ap.add_argument("--serve-pool", type=int, default=256, help=argparse.SUPPRESS)
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000", help=argparse.SUPPRESS)
     ap.add_argument("--pipeline-values", type=int, default=1 << 31, help=argparse.SUPPRESS)
     ap.add_argument("--batch-series", type=int, default=4096, help=argparse.SUPPRESS)
@@ -228,57 +234,79 @@ def clock_sampler(index: int):
 
 # ------------------------------------------------------------------------------ reference arm
 def run_reference(args):
-    """The CPU oracle (the method's plain definition) timed on the host, on a bounded sample
-    of the same workload; rank 0 only."""
+    """The CPU oracle (the method's plain definition) timed on the host cores (its threaded
+    driver over chunk ranges), on the same workload; rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import oracle
     from paper_2511_04140_gb300 import synth
     oracle.build()
-    sample = 1 << 18
-    a64 = synth.segments(args.n, seed=1)[:sample].copy()
-    a32 = synth.segments(args.n, seed=1, dtype=np.float32)[:sample].copy()
+    a64 = synth.segments(args.n, seed=1)
+    a32 = synth.segments(args.n, seed=1, dtype=np.float32)
     orig = a64.nbytes + a32.nbytes
+    cores = host_cores()
+    steps = max(1, min(args.steps, 5))               # each step is seconds of CPU work
 
     def step():
         for a in (a64, a32):
-            s = oracle.compress(a, BLOCK)
-            oracle.decompress(s)
+            s = oracle.compress(a, BLOCK, threads=cores)
+            oracle.decompress(s, threads=cores)
 
-    for _ in range(args.warmup):
+    for _ in range(min(args.warmup, 1)):
         step()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
-    dt = (time.perf_counter() - t0) / args.steps
+    dt = (time.perf_counter() - t0) / steps
     gbs = 2 * orig / dt / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64/int32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": args.n, "block": BLOCK, "sample_values_per_dtype": sample},
-            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": f"first {sample} values of the FP64 and of the FP32 array, "
-                                       "compress + decompress, single thread"},
+            "config": {"workload": WORKLOAD, "n": args.n, "block": BLOCK},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"the whole workload ({args.n} FP64 + {args.n} FP32 values), compress + "
+                                       f"decompress, {cores} threads over chunk ranges, {steps} steps"},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(n):
+def host_cores() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(host):
+    """The oracle on the host cores: one thread on the first 2^20 values of each array, and
+    every core (the oracle's threaded driver over chunk ranges) on the whole arrays."""
     from oracle import oracle
-    from paper_2511_04140_gb300 import synth
     oracle.build()
+    arrays = (host[np.float64], host[np.float32])
+    n = len(arrays[0])
+
+    def run(arrs, threads):
+        t0 = time.perf_counter()
+        for a in arrs:
+            st = oracle.compress(a, BLOCK, threads=threads)
+            oracle.decompress(st, threads=threads)
+        return time.perf_counter() - t0
+
     sample = 1 << 20
-    a64 = synth.segments(n, seed=1)[:sample].copy()
-    a32 = synth.segments(n, seed=1, dtype=np.float32)[:sample].copy()
-    t0 = time.perf_counter()
-    for a in (a64, a32):
-        s = oracle.compress(a, BLOCK)
-        oracle.decompress(s)
-    dt = time.perf_counter() - t0
-    return {"value": 2 * (a64.nbytes + a32.nbytes) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {sample} values of the FP64 and of the FP32 array (1/64 of the workload), "
-                      f"compress + decompress, single thread, {dt:.1f} s"}
+    part = [a[:sample].copy() for a in arrays]
+    dt1 = run(part, 1)
+    cores = host_cores()
+    dtn = run(arrays, cores)
+    orig_part = sum(a.nbytes for a in part)
+    orig = sum(a.nbytes for a in arrays)
+    return {"value": 2 * orig / dtn / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"the whole workload ({n} FP64 + {n} FP32 values), compress + decompress, "
+                      f"{cores} threads over chunk ranges, {dtn:.1f} s",
+            "single_thread": {"value": 2 * orig_part / dt1 / 1e9, "unit": "GB/s", "cores": 1,
+                              "sample": f"first {sample} values of the FP64 and of the FP32 array, "
+                                        f"compress + decompress, {dt1:.1f} s"}}
 
 
 def release_caches(torch):
@@ -474,9 +502,16 @@ def main():
     if rank == 0 and not args.no_e2e:
         progress("end-to-end pipeline")
         line["e2e"] = e2e(falcon, torch, bufs, host, dev, args)
-    if rank == 0 and not args.no_batched:
-        del bufs, host
+    if rank == 0:
+        del bufs
         torch.cuda.empty_cache()
+    if rank == 0 and not args.no_case1:
+        progress("case-1 workload")
+        line["case1"] = bench_case1(falcon, torch, dev, n, peak)
+    if rank == 0 and not args.no_variants:
+        progress("codec variants")
+        line["variants"] = bench_variants(falcon, torch, dev, host)
+    if rank == 0 and not args.no_batched:
         progress("batched launch")
         line["batched"] = bench_batched(falcon, synth, torch, dev, args.batch_series)
     if rank == 0 and not args.no_pipeline:
@@ -484,13 +519,21 @@ def main():
         progress("host pipeline")
         line["pipeline"] = bench_pipeline(falcon, synth, torch, dev, args.pipeline_values)
         release_caches(torch)
+    if rank == 0 and not args.no_schedulers:
+        progress("pipeline schedulers")
+        line["schedulers"] = bench_schedulers(falcon, torch, dev)
+        release_caches(torch)
+    if rank == 0 and not args.no_sweeps:
+        progress("parameter sweeps")
+        line["sweeps"] = bench_sweeps(falcon, torch, dev, peak)
+        release_caches(torch)
     if rank == 0 and not args.no_serve:
         progress("server")
         line["serve"] = bench_serve(args, dev)
         release_caches(torch)
     if rank == 0 and not args.no_cpu_baseline:
         progress("cpu baseline")
-        line["cpu_baseline"] = cpu_baseline(n)
+        line["cpu_baseline"] = cpu_baseline(host)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -604,6 +647,15 @@ def bench_batched(falcon, synth, torch, dev, count):
            "latency_note": "per-series completion time of compression from the start of the pass; "
                            "a batched launch completes every series at its end"}
     out["speedup"] = out["batched"]["gbs"] / out["plain"]["gbs"]
+    # every series' stream against the oracle's (threaded driver, host cores)
+    from oracle import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    eq = True
+    for x, st in zip(xs, streams):
+        eq &= st.cpu().numpy().tobytes() == oracle.compress(x.cpu().numpy(), block, threads=host_cores())
+    out["oracle_equal"] = bool(eq)
+    out["oracle_check"] = f"all {count} series' streams against the oracle's, {time.perf_counter() - t0:.0f} s"
     comp.close()
     dec.close()
     falcon.set_launch_config(0, 0)
@@ -617,23 +669,25 @@ def bench_serve(args, dev):
     at a time.  Each load runs for --serve-seconds (shortened from 60 s to keep the bench
     within minutes).  Latency: scheduled arrival -> result seen by the client."""
     from paper_2511_04140_gb300 import serve
-    pool = serve.make_pool(count=32, device=dev)
+    pool = serve.make_pool(count=args.serve_pool, device=dev)
     progress(f"server: pool of {len(pool)} requests built")
     rates = [float(r) for r in args.serve_rates.split(",")]
+    window = lambda r: args.serve_seconds if r <= 5000 else args.serve_seconds_saturated
     out = {"workload": f"{len(pool)}-request pool, sizes log-uniform 4 KB..256 MB, FP64/FP32 50/50, "
-                       f"50/50 compress/decompress, Poisson arrivals, {args.serve_seconds:g} s per load",
+                       f"50/50 compress/decompress, Poisson arrivals; {args.serve_seconds:g} s per load up to "
+                       f"5k req/s, {args.serve_seconds_saturated:g} s above (saturated)",
            "budget_bytes": 64 << 30, "loads": []}
     with serve.Server(budget_bytes=64 << 30, host_budget_bytes=16 << 30, device=dev) as srv:
         serve.run_load(srv, pool, rate=500, duration=0.3, seed=99)              # warm-up
         for rate in rates:
-            out["loads"].append({"offered_req_s": rate,
-                                 "server": serve.run_load(srv, pool, rate=rate, duration=args.serve_seconds,
+            out["loads"].append({"offered_req_s": rate, "seconds": window(rate),
+                                 "server": serve.run_load(srv, pool, rate=rate, duration=window(rate),
                                                           seed=int(rate))})
             progress(f"server: {rate:g} req/s done")
     serve.run_one_at_a_time(pool, rate=500, duration=0.3, seed=99, device=dev)   # warm-up
     for ld in out["loads"]:
         rate = ld["offered_req_s"]
-        ld["one_at_a_time"] = serve.run_one_at_a_time(pool, rate=rate, duration=args.serve_seconds, seed=int(rate),
+        ld["one_at_a_time"] = serve.run_one_at_a_time(pool, rate=rate, duration=window(rate), seed=int(rate),
                                                       device=dev)
         ld["gbs_vs_one_at_a_time"] = ld["server"]["gbs"] / ld["one_at_a_time"]["gbs"]
         progress(f"one at a time: {rate:g} req/s done")
@@ -698,12 +752,13 @@ def bench_pipeline(falcon, synth, torch, dev, n):
     vals = torch.where(mask, x * torch.pow(10.0, torch.rand(n, generator=g, device=dev, dtype=torch.float64) * 5 + 3), vals)
     del x, mask
     t0 = time.perf_counter()
-    h = torch.empty(n, dtype=torch.float64).pin_memory()
+    h = torch.empty(n, dtype=torch.float64, pin_memory=True)
     h.copy_(vals)
     del vals
     torch.cuda.empty_cache()
-    out = torch.empty(((n + (1 << 23) - 1) >> 23) * falcon.bound(1 << 23, falcon.F64, BLOCK), dtype=torch.uint8).pin_memory()
-    back = torch.empty(n, dtype=torch.float64).pin_memory()
+    out = torch.empty(((n + (1 << 23) - 1) >> 23) * falcon.bound(1 << 23, falcon.F64, BLOCK), dtype=torch.uint8,
+                      pin_memory=True)
+    back = torch.empty(n, dtype=torch.float64, pin_memory=True)
     setup_s = time.perf_counter() - t0
     # one untimed pass over the whole buffers (the first pass over fresh page-locked memory
     # runs 2-3x slower), then the median of three timed passes per direction
@@ -719,6 +774,20 @@ def bench_pipeline(falcon, synth, torch, dev, n):
         tds.append(time.perf_counter() - t0)
     tc, td = statistics.median(tcs), statistics.median(tds)
     ok = bool(torch.equal(y.view(torch.int64), h.view(torch.int64)))
+    # frames against the oracle: the first and last two, every 32nd, and the frames around
+    # the 4 GiB output offset (64-bit offsets in the host pipeline)
+    from oracle import oracle
+    oracle.build()
+    fv = 1 << 23
+    starts = np.concatenate([[0], np.cumsum(np.array(fb, dtype=np.int64))])
+    cross = int(np.searchsorted(starts, 1 << 32))
+    pick = sorted({0, 1, len(fb) - 2, len(fb) - 1, cross - 2, cross - 1, cross, *range(0, len(fb), 32)} &
+                  set(range(len(fb))))
+    blob = s.numpy()
+    eq = True
+    for f in pick:
+        part = h[f * fv:(f + 1) * fv].numpy()
+        eq &= blob[starts[f]:starts[f + 1]].tobytes() == oracle.compress(part, BLOCK, threads=host_cores())
     link = host_link(torch, dev)
     nbytes = n * 8
     return {"workload": f"{n} FP64 values ({nbytes / 2**30:.1f} GiB) in pinned host memory, random walk, "
@@ -726,10 +795,216 @@ def bench_pipeline(falcon, synth, torch, dev, n):
             "compress_gbs": nbytes / tc / 1e9, "decompress_gbs": nbytes / td / 1e9, "ratio": s.numel() / nbytes,
             "compress_gbs_samples": [round(nbytes / t / 1e9, 1) for t in tcs],
             "decompress_gbs_samples": [round(nbytes / t / 1e9, 1) for t in tds],
-            "frames": len(fb), "bit_exact": ok, "host_link_gbs": link,
+            "frames": len(fb), "bit_exact": ok, "host_link_gbs": link, "oracle_equal": bool(eq),
+            "oracle_frames": f"{len(pick)} frames: first, last, every 32nd and frames {cross - 2}..{cross} "
+                             "around the 4 GiB output offset",
             "compress_frac_of_h2d": nbytes / tc / 1e9 / link["h2d"],
             "decompress_frac_of_d2h": nbytes / td / 1e9 / link["d2h"], "setup_s": setup_s}
 
 
 if __name__ == "__main__":
     main()
+
+
+# ------------------------------------------------------------------------------ more sections
+def time_codec(falcon, torch, x, block, reps=5, variant=0):
+    """Kernel times (CUDA events, mean of `reps` after one warm-up) of compressing x with a
+    codec variant and decompressing the result, inputs resident; returns the times, the
+    stream (device) and whether the round trip is bit-exact."""
+    dev = x.device
+    code = falcon._dtype_code(x)
+    n = x.numel()
+    nc = (n + block - 1) // block
+    out = torch.empty(max(falcon.variant_bound(n, code, block, variant), 32), dtype=torch.uint8, device=dev)
+    ws = torch.zeros(falcon.workspace_bytes(nc), dtype=torch.uint8, device=dev)
+    rc = torch.zeros(2, dtype=torch.int64, device=dev)
+    rd = torch.zeros(2, dtype=torch.int64, device=dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+    falcon.compress_variant_async(x, block, variant, out, ws, rc, stream)
+    torch.cuda.synchronize(dev)
+    nbytes = int(rc[0].item())
+    hdr = out[:32].cpu().numpy().tobytes()
+    falcon.decompress_async(out, nbytes, hdr, y, ws, rd, stream)
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tc = td = 0.0
+    for _ in range(reps):
+        ev[0].record(stream)
+        falcon.compress_variant_async(x, block, variant, out, ws, rc, stream)
+        ev[1].record(stream)
+        falcon.decompress_async(out, nbytes, hdr, y, ws, rd, stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize(dev)
+        tc += ev[0].elapsed_time(ev[1])
+        td += ev[1].elapsed_time(ev[2])
+    iv = torch.int64 if x.dtype == torch.float64 else torch.int32
+    ok = int(rc[1].item()) == 0 and int(rd[1].item()) == 0 and torch.equal(y.view(iv), x.view(iv))
+    return tc / reps, td / reps, out[:nbytes], bool(ok)
+
+
+def decimal_segments(n, seed, dtype):
+    """The segment workload without outliers and special values: every chunk is Case 1 for
+    FP64 (decimals of at most 10 significant digits); FP32 chunks whose decimals exceed 7
+    significant digits take Case 2."""
+    from paper_2511_04140_gb300 import synth
+    return synth.segments(n, seed=seed, dtype=dtype, outlier_rate=0.0, special_rate=0.0)
+
+
+def bench_case1(falcon, torch, dev, n, peak):
+    """Case-1 path at HBM scale: the float-to-integer transform of Eq. 4 (alpha search, exact
+    scaling, exact division on decode) on 2^26 values without escapes."""
+    out = {"workload": f"decimal segments: {n} values, FP64 and FP32, 4096-value segments with 0..6 "
+                       "places, sinusoid + AR(1), no outliers and no special values; block 1024", "kernels": {}}
+    for dt in (np.float64, np.float32):
+        arr = decimal_segments(n, 7, dt)
+        x = torch.from_numpy(arr).to(dev)
+        tc, td, st, ok = time_codec(falcon, torch, x, BLOCK, reps=5)
+        name = "f64" if dt == np.float64 else "f32"
+        nb = st.numel()
+        hdr = st[:32 + 4 * ((n + BLOCK - 1) // BLOCK)].cpu().numpy()
+        recs = np.frombuffer(st.cpu().numpy().tobytes(), dtype=np.uint8)
+        sizes = hdr[32:].view("<u4")
+        offs = 32 + 4 * len(sizes) + np.concatenate([[0], np.cumsum(sizes[:-1], dtype=np.int64)])
+        alpha = recs[offs]
+        case1 = float(np.mean(alpha <= (22 if dt == np.float64 else 10)))
+        for kind, ms in (("compress", tc), ("decompress", td)):
+            alg = arr.nbytes + nb
+            out["kernels"][f"{kind}_{name}"] = {"ms": ms, "gbs_original": arr.nbytes / ms / 1e6,
+                                                "hbm_gbs": alg / ms / 1e6, "hbm_frac": alg / ms / 1e6 / peak}
+        out[f"ratio_{name}"] = nb / arr.nbytes
+        out[f"case1_chunks_{name}"] = case1
+        out[f"bit_exact_{name}"] = ok
+        del x, st
+    torch.cuda.empty_cache()
+    return out
+
+
+def oracle_equal_sampled(oracle, vals: np.ndarray, stream: bytes, block: int, chunks: int = 4096, variant: int = 0):
+    """The stream's first `chunks` records equal the oracle's records for the same values."""
+    nc = (len(vals) + block - 1) // block
+    k = min(nc, chunks)
+    ref = oracle.compress(vals[:k * block] if k < nc else vals, block, variant=variant, threads=host_cores())
+    rec_ref = oracle.chunk_records(ref)
+    sizes = np.frombuffer(stream, dtype="<u4", count=nc, offset=32)
+    pos = 32 + 4 * nc
+    for c in range(k):
+        sz = int(sizes[c])
+        if stream[pos:pos + sz] != rec_ref[c]:
+            return False
+        pos += sz
+    return True
+
+
+def bench_variants(falcon, torch, dev, host):
+    """The ablation of Sec. 5.4.2 (Fig. 12b): Falcon against Fal._Sparse, Fal._Dense and
+    Fal._Elf on the random walk (1,048,576 FP64 values, 2 places) and the segment workload
+    (2^26 values, FP64 and FP32): ratio and kernel GB/s per variant; each variant's stream is
+    checked against the oracle's on its first 4096 chunks and decoded bit-exactly."""
+    from oracle import oracle
+    from paper_2511_04140_gb300 import synth
+    oracle.build()
+    names = {0: "falcon", 1: "fal_sparse", 2: "fal_dense", 3: "fal_elf"}
+    works = [("random_walk_f64", synth.random_walk(1 << 20, seed=0, places=2)),
+             ("segments_f64", host[np.float64]), ("segments_f32", host[np.float32])]
+    out = {"workloads": {}}
+    for wname, arr in works:
+        x = torch.from_numpy(arr).to(dev)
+        rows = {}
+        for v, vname in names.items():
+            tc, td, st, ok = time_codec(falcon, torch, x, BLOCK, reps=3, variant=v)
+            blob = st.cpu().numpy().tobytes()
+            rows[vname] = {"ratio": len(blob) / arr.nbytes, "compress_gbs": arr.nbytes / tc / 1e6,
+                           "decompress_gbs": arr.nbytes / td / 1e6, "compress_ms": tc, "decompress_ms": td,
+                           "bit_exact": ok, "oracle_equal": oracle_equal_sampled(oracle, arr, blob, BLOCK, variant=v)}
+        out["workloads"][wname] = rows
+        del x
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_schedulers(falcon, torch, dev, n=1 << 28):
+    """The scheduler ablation of Sec. 5.4.1 (Fig. 12a): event-driven, sync-based and
+    pre-allocation compression of 2 GiB of host values (the host-pipeline generator) in
+    64 MiB frames with 1..32 streams; every output equals the event-driven one."""
+    g = torch.Generator(device=dev)
+    g.manual_seed(6)
+    from paper_2511_04140_gb300 import synth
+    vals = synth.random_walk_cuda(n, g, places=3, outlier_rate=0.005, device=dev)
+    h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    h.copy_(vals)
+    del vals
+    fv = 1 << 23
+    cap = ((n + fv - 1) // fv) * falcon.bound(fv, falcon.F64, BLOCK)
+    outs = {sch: torch.empty(cap, dtype=torch.uint8, pin_memory=True) for sch in (0, 1, 2)}
+    ref = None
+    res = {"workload": f"{n} FP64 values ({n * 8 / 2**30:.0f} GiB) in pinned host memory, random walk, 3 places, "
+                       "0.5% outliers; 64 MiB frames", "gbs": {}}
+    names = {0: "event_driven", 1: "sync_based", 2: "pre_allocation"}
+    ok = True
+    for sch, nm in names.items():
+        res["gbs"][nm] = {}
+        for ns in (1, 2, 4, 8, 16, 32):
+            falcon.pipeline_compress(h, block=BLOCK, frame_values=fv, nstreams=ns, out=outs[sch], scheduler=sch)
+            t0 = time.perf_counter()
+            s, fb = falcon.pipeline_compress(h, block=BLOCK, frame_values=fv, nstreams=ns, out=outs[sch], scheduler=sch)
+            dt = time.perf_counter() - t0
+            res["gbs"][nm][str(ns)] = n * 8 / dt / 1e9
+            if ref is None:
+                ref = (s.clone(), fb)
+            else:
+                ok &= fb == ref[1] and torch.equal(s, ref[0])
+    res["bit_exact"] = bool(ok)
+    return res
+
+
+def bench_sweeps(falcon, torch, dev, peak):
+    """Parameter sweeps of Sec. 5.3 on synthetic data: decimal places (Fig. 10's beta sweep:
+    2^24 FP64 random-walk values rounded to 0..15 places, kernel GB/s and ratio), data size
+    (Fig. 11: 100 MB .. 16 GiB through the host pipeline) and frame size (Table 5:
+    0.5 .. 8 x 1025 x 1024 values per frame, 2 GiB)."""
+    from paper_2511_04140_gb300 import synth
+    out = {"places": {}, "data_size": {}, "frame_size": {}}
+    g = torch.Generator(device=dev)
+    g.manual_seed(8)
+    n = 1 << 24
+    for pl in range(16):
+        x = synth.random_walk_cuda(n, g, places=pl, device=dev)
+        tc, td, st, ok = time_codec(falcon, torch, x, BLOCK, reps=3)
+        out["places"][str(pl)] = {"ratio": st.numel() / (n * 8), "compress_gbs": n * 8 / tc / 1e6,
+                                  "decompress_gbs": n * 8 / td / 1e6, "bit_exact": ok}
+    del x
+    big = 1 << 31
+    vals = synth.random_walk_cuda(big, g, places=3, outlier_rate=0.005, device=dev)
+    h = torch.empty(big, dtype=torch.float64, pin_memory=True)
+    h.copy_(vals)
+    del vals
+    torch.cuda.empty_cache()
+    fv = 1 << 23
+    out_buf = torch.empty(((big + fv - 1) // fv) * falcon.bound(fv, falcon.F64, BLOCK), dtype=torch.uint8,
+                          pin_memory=True)
+    for mb in (100, 300, 700, 2048, 8192, 16384):
+        m = min(big, mb * (1 << 20) // 8)
+        part = h[:m]
+        falcon.pipeline_compress(part, block=BLOCK, frame_values=fv, out=out_buf)
+        t0 = time.perf_counter()
+        s, fb = falcon.pipeline_compress(part, block=BLOCK, frame_values=fv, out=out_buf)
+        tcp = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        falcon.pipeline_decompress(s, fb)
+        tdp = time.perf_counter() - t0
+        out["data_size"][f"{mb}MB"] = {"compress_gbs": m * 8 / tcp / 1e9, "decompress_gbs": m * 8 / tdp / 1e9}
+    part = h[:1 << 28]
+    for mult in (0.5, 1, 2, 4, 8):
+        fvm = int(mult * 1025 * 1024)
+        falcon.pipeline_compress(part, block=BLOCK, frame_values=fvm, out=out_buf)
+        t0 = time.perf_counter()
+        s, fb = falcon.pipeline_compress(part, block=BLOCK, frame_values=fvm, out=out_buf)
+        tcp = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        falcon.pipeline_decompress(s, fb)
+        tdp = time.perf_counter() - t0
+        out["frame_size"][f"{mult}x1025x1024"] = {"compress_gbs": part.numel() * 8 / tcp / 1e9,
+                                                  "decompress_gbs": part.numel() * 8 / tdp / 1e9}
+    del h, out_buf
+    return out

@@ -229,7 +229,7 @@ int falcon_batch_forget(void *d_workspace);
  * streams.  As in the paper's event-driven scheduler, a frame's place in the output is
  * fixed in launch order as soon as its compressed size has come back (the "M-D2H"), so the
  * payload copy ("P-D2H") of frame f overlaps the upload and compression of later frames and
- * the output needs no merging pass.  Every frame is a complete stream; the frames are
+ * the output needs no merging pass.  Frames are taken by whichever stream is idle.  Every frame is a complete stream; the frames are
  * concatenated in h_out.  Host buffers should be page-locked (cudaHostAlloc) for the copies
  * to overlap; pageable memory works but serialises them.  The device buffers
  * (nstreams x (frame input + frame bound + workspace)) are allocated on first use, kept per
@@ -243,6 +243,30 @@ int falcon_batch_forget(void *d_workspace);
 int falcon_pipeline_compress(const void *h_in, uint64_t n, int dtype, uint32_t block_size,
                              uint64_t frame_values, int nstreams, void *h_out, size_t out_capacity,
                              uint64_t *h_frame_bytes, size_t *out_bytes);
+
+/* The three compression schedulers of Sec. 3.1 (Fig. 5), for the ablation of Sec. 5.4.1
+ * (Fig. 12a); all write the same bytes:
+ *   FALCON_SCHED_EVENT_DRIVEN   Alg. 1 (falcon_pipeline_compress): each frame's size comes back
+ *                               first (M-D2H), frames are placed in launch order as their
+ *                               sizes arrive and their payload copies (P-D2H) overlap later
+ *                               frames; any idle stream takes the next frame;
+ *   FALCON_SCHED_SYNC_BASED     the host waits for a frame's size before it launches the next
+ *                               frame: only the payload copy overlaps the next frame's work;
+ *   FALCON_SCHED_PRE_ALLOCATION every frame is copied back whole from a fixed output slot of
+ *                               the worst-case size (falcon_bound of a frame) into page-locked
+ *                               staging memory kept by the library, then merged into h_out in
+ *                               frame order by the host. */
+typedef enum {
+    FALCON_SCHED_EVENT_DRIVEN = 0,
+    FALCON_SCHED_SYNC_BASED = 1,
+    FALCON_SCHED_PRE_ALLOCATION = 2
+} falcon_scheduler;
+
+/* falcon_pipeline_compress with a chosen scheduler (same arguments and results;
+ * FALCON_ERR_INVALID for an unknown scheduler). */
+int falcon_pipeline_compress_with(const void *h_in, uint64_t n, int dtype, uint32_t block_size,
+                                  uint64_t frame_values, int nstreams, int scheduler, void *h_out,
+                                  size_t out_capacity, uint64_t *h_frame_bytes, size_t *out_bytes);
 
 /* Decompresses nframes concatenated streams (lengths in h_frame_bytes) from h_in into h_out.
  * Output positions follow from the frame headers, so frames are processed fully in

@@ -1,17 +1,25 @@
 // Host <-> device streaming pipeline (Sec. 3.1, Alg. 1 of the paper): host code only.
 //
-// Compression follows the event-driven scheduler: every CUDA stream slot cycles through
-//   Idle   -> H2D(frame) ; compress (async) ; D2H(16-byte result) ; event      -> MPend
-//   MPend  -> (when this frame is the next one to be placed and its event fired)
-//             offset fixed ; D2H(payload -> h_out + offset) ; event            -> PPend
-//   PPend  -> (event fired)                                                    -> Idle
-// Frames are launched round-robin on the slots, so launch order = frame order and the
-// slot holding the next frame to be placed is simply frame % nstreams.
+// Compression runs one of the three schedulers of Sec. 3.1 (Fig. 5), on nstreams CUDA
+// stream slots; each frame is a complete stream and the output is the frames in order:
+//   event-driven (Alg. 1, the paper's choice): every slot cycles through
+//     Idle   -> H2D(frame) ; compress (async) ; D2H(16-byte result) ; event      -> MPend
+//     MPend  -> (when this frame is the next one to be placed and its event fired)
+//               offset fixed ; D2H(payload -> h_out + offset) ; event            -> PPend
+//     PPend  -> (event fired)                                                    -> Idle
+//     Frames go to whichever slot is idle, in frame order; offsets are fixed in that order.
+//   sync-based: the host waits for each frame's size (M-D2H) before it launches the next
+//     frame; only the payload copy (P-D2H) of a frame overlaps the next frame's upload and
+//     kernel.
+//   pre-allocation: every frame's output goes to a fixed slot of the worst-case size; the
+//     whole slot is copied back (bytes past the stream included), then the host merges the
+//     frames into h_out in order.
 // Decompression knows every frame's output position from its header (pre-allocation), so
 // each slot runs H2D -> decompress -> D2H without ordering between slots.
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "falcon.h"
@@ -28,6 +36,8 @@ struct Slot {
     uint8_t *d_ws = nullptr;
     uint64_t *d_res = nullptr;
     uint64_t *h_res = nullptr;        // pinned
+    uint8_t *h_stage = nullptr;       // pinned, pre-allocation scheduler only
+    size_t stage_bytes = 0;
     cudaEvent_t ev = nullptr;
     SlotState state = kIdle;
     uint64_t frame = 0;
@@ -45,6 +55,7 @@ struct SlotSet {
             cudaFree(s.d_ws);
             cudaFree(s.d_res);
             if (s.h_res) cudaFreeHost(s.h_res);
+            if (s.h_stage) cudaFreeHost(s.h_stage);
         }
     }
     int init(int n, size_t in_bytes, size_t out_bytes, size_t ws_bytes) {
@@ -121,69 +132,129 @@ extern "C" {
 int falcon_pipeline_compress(const void *h_in, uint64_t n, int dtype, uint32_t block_size, uint64_t frame_values,
                              int nstreams, void *h_out, size_t out_capacity, uint64_t *h_frame_bytes,
                              size_t *out_bytes) {
+    return falcon_pipeline_compress_with(h_in, n, dtype, block_size, frame_values, nstreams,
+                                         FALCON_SCHED_EVENT_DRIVEN, h_out, out_capacity, h_frame_bytes, out_bytes);
+}
+
+int falcon_pipeline_compress_with(const void *h_in, uint64_t n, int dtype, uint32_t block_size,
+                                  uint64_t frame_values, int nstreams, int scheduler, void *h_out,
+                                  size_t out_capacity, uint64_t *h_frame_bytes, size_t *out_bytes) {
     if ((dtype != FALCON_F64 && dtype != FALCON_F32) || !h_out || !out_bytes || !h_frame_bytes) return FALCON_ERR_INVALID;
     if (n > 0 && !h_in) return FALCON_ERR_INVALID;
     if (frame_values == 0 || nstreams < 1 || nstreams > 256) return FALCON_ERR_INVALID;
+    if (scheduler < FALCON_SCHED_EVENT_DRIVEN || scheduler > FALCON_SCHED_PRE_ALLOCATION) return FALCON_ERR_INVALID;
     if (falcon_bound(frame_values, dtype, block_size) == 0) return FALCON_ERR_INVALID;
     const size_t s = dtype == FALCON_F64 ? 8 : 4;
     const uint64_t nframes = (n + frame_values - 1) / frame_values;
     const uint64_t fchunks = (frame_values + block_size - 1) / block_size;
     const size_t fbound = falcon_bound(frame_values, dtype, block_size);
+    const size_t ws_bytes = falcon_workspace_bytes(fchunks);
     std::unique_lock<std::mutex> hold;
     SlotSet *setp = nullptr;
     const int want = (int)(nframes < (uint64_t)nstreams ? (nframes ? nframes : 1) : (uint64_t)nstreams);
-    int st = acquire_slots(want, frame_values * s, fbound, falcon_workspace_bytes(fchunks), hold, setp);
+    int st = acquire_slots(want, frame_values * s, fbound, ws_bytes, hold, setp);
     if (st) return st;
     SlotSet &set = *setp;
     const uint64_t ns = (uint64_t)want;
     const uint8_t *in8 = static_cast<const uint8_t *>(h_in);
     uint8_t *out8 = static_cast<uint8_t *>(h_out);
-    uint64_t next = 0, placed = 0, done = 0;
-    size_t offset = 0;
-    int status = FALCON_OK;
-    while (done < nframes) {
+    const bool prealloc = scheduler == FALCON_SCHED_PRE_ALLOCATION;
+    if (prealloc) {
         for (uint64_t i = 0; i < ns; ++i) {
             Slot &sl = set.slots[i];
-            if (sl.state == kIdle) {
-                if (next < nframes && next % ns == i && status == FALCON_OK) {
-                    const uint64_t first = next * frame_values;
-                    const uint64_t m = (n - first) < frame_values ? (n - first) : frame_values;
-                    if (cudaMemcpyAsync(sl.d_in, in8 + first * s, m * s, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
-                        return FALCON_ERR_CUDA;
-                    st = falcon_compress_async(sl.d_in, m, dtype, block_size, sl.d_out, fbound, sl.d_ws,
-                                               falcon_workspace_bytes(fchunks), sl.d_res, sl.stream);
-                    if (st) return st;
-                    if (cudaMemcpyAsync(sl.h_res, sl.d_res, 16, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
-                        return FALCON_ERR_CUDA;
-                    if (cudaEventRecord(sl.ev, sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
-                    sl.frame = next++;
-                    sl.state = kMPend;
-                }
-            } else if (sl.state == kMPend) {
-                if (sl.frame != placed) continue;                 // offsets are fixed in launch order
-                const cudaError_t q = cudaEventQuery(sl.ev);
-                if (q == cudaErrorNotReady) continue;
-                if (q != cudaSuccess) return FALCON_ERR_CUDA;
-                const uint64_t cs = sl.h_res[0];
-                if (sl.h_res[1] != 0 && status == FALCON_OK) status = (int)sl.h_res[1];
-                if (status == FALCON_OK && offset + cs > out_capacity) status = FALCON_ERR_CAPACITY;
-                h_frame_bytes[sl.frame] = cs;
-                if (status == FALCON_OK &&
-                    cudaMemcpyAsync(out8 + offset, sl.d_out, cs, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
-                    return FALCON_ERR_CUDA;
-                if (cudaEventRecord(sl.ev, sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
-                offset += cs;
-                ++placed;
-                sl.state = kPPend;
-            } else {
-                const cudaError_t q = cudaEventQuery(sl.ev);
-                if (q == cudaErrorNotReady) continue;
-                if (q != cudaSuccess) return FALCON_ERR_CUDA;
-                sl.state = kIdle;
-                ++done;
+            if (sl.stage_bytes < fbound) {
+                if (sl.h_stage) cudaFreeHost(sl.h_stage);
+                sl.h_stage = nullptr;
+                sl.stage_bytes = 0;
+                if (cudaHostAlloc(&sl.h_stage, fbound, cudaHostAllocDefault) != cudaSuccess) return FALCON_ERR_CUDA;
+                sl.stage_bytes = fbound;
             }
         }
-        if (status != FALCON_OK && placed == next) break;       // nothing left in flight to place
+    }
+    // launch: upload, kernels and the result words (pre-allocation: the whole output slot)
+    auto launch = [&](Slot &sl, uint64_t f) -> int {
+        const uint64_t first = f * frame_values;
+        const uint64_t m = (n - first) < frame_values ? (n - first) : frame_values;
+        if (cudaMemcpyAsync(sl.d_in, in8 + first * s, m * s, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+            return FALCON_ERR_CUDA;
+        const int r = falcon_compress_async(sl.d_in, m, dtype, block_size, sl.d_out, fbound, sl.d_ws, ws_bytes,
+                                            sl.d_res, sl.stream);
+        if (r) return r;
+        if (cudaMemcpyAsync(sl.h_res, sl.d_res, 16, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+            return FALCON_ERR_CUDA;
+        if (prealloc && cudaMemcpyAsync(sl.h_stage, sl.d_out, fbound, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+            return FALCON_ERR_CUDA;
+        if (cudaEventRecord(sl.ev, sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+        sl.frame = f;
+        sl.state = kMPend;
+        return FALCON_OK;
+    };
+    size_t offset = 0;
+    int status = FALCON_OK;
+    // places frame sl.frame (its size is back): records it and fixes its offset
+    auto place = [&](Slot &sl) -> size_t {
+        const uint64_t cs = sl.h_res[0];
+        if (sl.h_res[1] != 0 && status == FALCON_OK) status = (int)sl.h_res[1];
+        if (status == FALCON_OK && offset + cs > out_capacity) status = FALCON_ERR_CAPACITY;
+        h_frame_bytes[sl.frame] = cs;
+        return cs;
+    };
+    if (scheduler == FALCON_SCHED_SYNC_BASED) {
+        for (uint64_t f = 0; f < nframes && status == FALCON_OK; ++f) {
+            Slot &sl = set.slots[f % ns];
+            if (cudaStreamSynchronize(sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;   // its last payload copy
+            if ((st = launch(sl, f))) return st;
+            if (cudaEventSynchronize(sl.ev) != cudaSuccess) return FALCON_ERR_CUDA;         // M-D2H: the size
+            const size_t cs = place(sl);
+            if (status == FALCON_OK &&
+                cudaMemcpyAsync(out8 + offset, sl.d_out, cs, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+                return FALCON_ERR_CUDA;
+            offset += cs;
+        }
+    } else {
+        uint64_t next = 0, placed = 0, done = 0;   // frames launched / placed / finished
+        while (done < next || (next < nframes && status == FALCON_OK)) {
+            bool progress = false;
+            for (uint64_t i = 0; i < ns; ++i) {
+                Slot &sl = set.slots[i];
+                if (sl.state == kIdle) {
+                    if (next < nframes && status == FALCON_OK && next - placed < ns) {
+                        if ((st = launch(sl, next))) return st;
+                        ++next;
+                        progress = true;
+                    }
+                } else if (sl.state == kMPend) {
+                    if (sl.frame != placed) continue;                 // offsets are fixed in launch order
+                    const cudaError_t q = cudaEventQuery(sl.ev);
+                    if (q == cudaErrorNotReady) continue;
+                    if (q != cudaSuccess) return FALCON_ERR_CUDA;
+                    const size_t cs = place(sl);
+                    if (prealloc) {
+                        // the merge step: the frame's bytes from its fixed slot into place
+                        if (status == FALCON_OK) std::memcpy(out8 + offset, sl.h_stage, cs);
+                        sl.state = kIdle;
+                        ++done;
+                    } else {
+                        if (status == FALCON_OK &&
+                            cudaMemcpyAsync(out8 + offset, sl.d_out, cs, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+                            return FALCON_ERR_CUDA;
+                        if (cudaEventRecord(sl.ev, sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+                        sl.state = kPPend;
+                    }
+                    offset += cs;
+                    ++placed;
+                    progress = true;
+                } else {
+                    const cudaError_t q = cudaEventQuery(sl.ev);
+                    if (q == cudaErrorNotReady) continue;
+                    if (q != cudaSuccess) return FALCON_ERR_CUDA;
+                    sl.state = kIdle;
+                    ++done;
+                    progress = true;
+                }
+            }
+            if (!progress) std::this_thread::yield();
+        }
     }
     for (uint64_t i = 0; i < ns; ++i)
         if (cudaStreamSynchronize(set.slots[i].stream) != cudaSuccess) return FALCON_ERR_CUDA;

@@ -23,6 +23,8 @@ MAX_BLOCK = 1025
 _lock = threading.Lock()
 _lib = None
 COMPRESS, DECOMPRESS = 0, 1
+# compression schedulers of the host pipeline (falcon_scheduler, Sec. 3.1)
+SCHED_EVENT_DRIVEN, SCHED_SYNC_BASED, SCHED_PRE_ALLOCATION = 0, 1, 2
 # codec variants (falcon_variant): Falcon and the ablations of Sec. 5.4.2
 VARIANT_FALCON, VARIANT_SPARSE, VARIANT_DENSE, VARIANT_ELF = 0, 1, 2, 3
 
@@ -99,6 +101,8 @@ def _load():
             L.falcon_set_launch_config.argtypes = [ci, ci]
             L.falcon_pipeline_compress.restype = ci
             L.falcon_pipeline_compress.argtypes = [vp, u64, ci, u32, u64, ci, vp, sz, vp, c.POINTER(sz)]
+            L.falcon_pipeline_compress_with.restype = ci
+            L.falcon_pipeline_compress_with.argtypes = [vp, u64, ci, u32, u64, ci, ci, vp, sz, vp, c.POINTER(sz)]
             L.falcon_pipeline_decompress.restype = ci
             L.falcon_pipeline_decompress.argtypes = [vp, vp, u64, ci, vp, sz, c.POINTER(u64)]
             L.falcon_compress_noalloc.restype = ci
@@ -329,9 +333,10 @@ class Batch:
 
 
 def pipeline_compress(x: torch.Tensor, block: int = 1024, frame_values: int = 1 << 23, nstreams: int = 16,
-                      out: torch.Tensor | None = None):
+                      out: torch.Tensor | None = None, scheduler: int = 0):
     """Streams a HOST tensor (pin it for overlap) through the GPU in frames; returns
-    (uint8 host tensor of the concatenated frame streams, list of frame lengths)."""
+    (uint8 host tensor of the concatenated frame streams, list of frame lengths).
+    scheduler: SCHED_EVENT_DRIVEN (the paper's), SCHED_SYNC_BASED or SCHED_PRE_ALLOCATION."""
     if x.is_cuda or not x.is_contiguous():
         raise ValueError("x must be a contiguous host tensor")
     code = _dtype_code(x)
@@ -342,8 +347,9 @@ def pipeline_compress(x: torch.Tensor, block: int = 1024, frame_values: int = 1 
         out = torch.empty(cap, dtype=torch.uint8, pin_memory=torch.cuda.is_available())
     fb = (ctypes.c_uint64 * max(nframes, 1))()
     total = ctypes.c_size_t()
-    _check(_load().falcon_pipeline_compress(x.data_ptr(), n, code, block, frame_values, nstreams, out.data_ptr(),
-                                            out.numel(), fb, ctypes.byref(total)), "pipeline_compress")
+    _check(_load().falcon_pipeline_compress_with(x.data_ptr(), n, code, block, frame_values, nstreams, scheduler,
+                                                 out.data_ptr(), out.numel(), fb, ctypes.byref(total)),
+           "pipeline_compress")
     return out[:total.value], [int(fb[i]) for i in range(nframes)]
 
 

@@ -251,23 +251,25 @@ def run_one_at_a_time(pool, rate: float, duration: float, seed: int = 0, device=
     return _summary(lat, nbytes, wall, len(arr))
 
 
-def make_pool(count: int = 64, seed: int = 5, min_bytes: int = 4 << 10, max_bytes: int = 256 << 20,
+def make_pool(count: int = 256, seed: int = 5, min_bytes: int = 4 << 10, max_bytes: int = 256 << 20,
               device="cuda", block: int = 1024):
     """Request pool: sizes log-uniform in [min_bytes, max_bytes], FP64/FP32 50/50, random-walk
-    data (2 places); half compress requests (values) and half decompress requests (streams
-    produced by the library).  Payloads live in pinned host memory."""
+    data (2 places, generated on the GPU); half compress requests (values) and half
+    decompress requests (streams produced by the library).  Payloads live in pinned host
+    memory."""
     from . import synth
     rng = np.random.default_rng(seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
     pool = []
     for i in range(count):
         nbytes = int(np.exp(rng.uniform(np.log(min_bytes), np.log(max_bytes))))
         dtype = np.float64 if rng.random() < 0.5 else np.float32
         n = max(1, nbytes // np.dtype(dtype).itemsize)
-        vals = synth.random_walk(n, seed=int(rng.integers(1 << 30)), places=2, dtype=dtype)
-        host = torch.from_numpy(vals).pin_memory()
+        vals = synth.random_walk_cuda(n, g, places=2, dtype=dtype, device=device)
         if i % 2 == 0:
-            pool.append((COMPRESS, host))
+            pool.append((COMPRESS, vals.cpu().pin_memory()))
         else:
-            s = falcon.compress(host.to(device), block)
-            pool.append((DECOMPRESS, s.cpu().pin_memory()))
+            pool.append((DECOMPRESS, falcon.compress(vals, block).cpu().pin_memory()))
+        del vals
     return pool

@@ -28,7 +28,7 @@ from fractions import Fraction
 
 import numpy as np
 
-__all__ = ["decimal_to_f64", "decimal_to_f32", "random_walk", "segments", "series_batch",
+__all__ = ["decimal_to_f64", "decimal_to_f32", "random_walk", "random_walk_cuda", "segments", "series_batch",
            "adversarial_f64", "adversarial_f32", "specials_f64", "specials_f32"]
 
 _P10 = np.array([10.0 ** k for k in range(23)], dtype=np.float64)   # exact for k <= 22
@@ -227,30 +227,39 @@ def series_batch_cuda(count: int = 4096, seed: int = 2, min_len: int = 1024, max
     rates = rng.uniform(0, max_outlier_rate, size=count)
     g = torch.Generator(device=device)
     g.manual_seed(seed)
-    out = []
-    for i in range(count):
-        n = int(lengths[i])
-        steps = torch.randn(n, generator=g, device=device, dtype=torch.float64) * 0.5
-        steps[0] = 0.0
-        x = 20.0 + torch.cumsum(steps, 0)
-        p = int(places[i])
-        k = torch.round(x * (10.0 ** p))
-        d = k / (10.0 ** p)                                  # exact operands: one rounding
-        if is64[i]:
-            vals = d
-        else:
-            vals = d.to(torch.float32)
-            bits = d.view(torch.int64)
-            exp = (bits >> 52) & 0x7FF
-            tie = ((bits & ((1 << 29) - 1)) == (1 << 28)) & (exp >= 1023 - 126) & (exp <= 1023 + 127)
-            idx = torch.nonzero(tie).flatten()
-            if idx.numel():
-                fixed = decimal_to_f32(k[idx].to(torch.int64).cpu().numpy(), p)
-                vals[idx] = torch.from_numpy(fixed).to(device)
-        mask = torch.rand(n, generator=g, device=device) < float(rates[i])
+    return [random_walk_cuda(int(lengths[i]), g, places=int(places[i]),
+                             dtype=np.float64 if is64[i] else np.float32, outlier_rate=float(rates[i]),
+                             device=device) for i in range(count)]
+
+
+def random_walk_cuda(n: int, generator, places: int = 2, dtype=np.float64, outlier_rate: float = 0.0,
+                     device="cuda"):
+    """``random_walk`` generated on the GPU from a torch Generator: x_{i+1} = x_i + N(0, 0.5)
+    from 20.0, rounded to ``places`` decimals (the nearest binary value of the decimal, FP32
+    ties resolved exactly), a fraction ``outlier_rate`` replaced by full-precision outliers
+    x * 10^U(3,8).  Returns a CUDA tensor."""
+    import torch
+    g = generator
+    steps = torch.randn(n, generator=g, device=device, dtype=torch.float64) * 0.5
+    steps[0] = 0.0
+    x = 20.0 + torch.cumsum(steps, 0)
+    k = torch.round(x * (10.0 ** places))
+    d = k / (10.0 ** places)                                 # exact operands: one rounding
+    if dtype == np.float64:
+        vals = d
+    else:
+        vals = d.to(torch.float32)
+        bits = d.view(torch.int64)
+        exp = (bits >> 52) & 0x7FF
+        tie = ((bits & ((1 << 29) - 1)) == (1 << 28)) & (exp >= 1023 - 126) & (exp <= 1023 + 127)
+        idx = torch.nonzero(tie).flatten()
+        if idx.numel():
+            fixed = decimal_to_f32(k[idx].to(torch.int64).cpu().numpy(), places)
+            vals[idx] = torch.from_numpy(fixed).to(device)
+    if outlier_rate > 0:
+        mask = torch.rand(n, generator=g, device=device) < float(outlier_rate)
         if bool(mask.any()):
             u = torch.rand(n, generator=g, device=device, dtype=torch.float64) * 5 + 3
             big = (x * torch.pow(10.0, u)).to(vals.dtype)
             vals = torch.where(mask, big, vals)
-        out.append(vals.contiguous())
-    return out
+    return vals.contiguous()

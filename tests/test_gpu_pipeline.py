@@ -62,3 +62,35 @@ def test_pipeline_capacity(F):
     with pytest.raises(F.FalconError) as e:
         F.pipeline_compress(x, block=1024, frame_values=50_000, nstreams=4, out=out)
     assert e.value.status == F.ERR_CAPACITY
+
+
+@pytest.mark.parametrize("scheduler", [1, 2])
+@pytest.mark.parametrize("nstreams", [1, 2, 5, 16])
+def test_schedulers_write_the_event_driven_bytes(F, oracle, scheduler, nstreams):
+    """Sec. 3.1's sync-based and pre-allocation schedulers (the ablation of Sec. 5.4.1) give
+    the same frames as the event-driven one, each equal to the oracle's stream."""
+    vals = synth.segments(520_003, seed=14)
+    frame = 65_536
+    x = torch.from_numpy(vals).pin_memory()
+    ref, fb_ref = F.pipeline_compress(x, block=1024, frame_values=frame, nstreams=nstreams)
+    s, fb = F.pipeline_compress(x, block=1024, frame_values=frame, nstreams=nstreams, scheduler=scheduler)
+    assert fb == fb_ref
+    assert torch.equal(s, ref)
+    blob = s.numpy().tobytes()
+    off = 0
+    for i, nb in enumerate(fb):
+        assert blob[off:off + nb] == oracle.compress(vals[i * frame:(i + 1) * frame], 1024), i
+        off += nb
+
+
+def test_scheduler_capacity_and_unknown(F):
+    vals = synth.segments(200_000, seed=3)
+    x = torch.from_numpy(vals).pin_memory()
+    out = torch.empty(100_000, dtype=torch.uint8).pin_memory()
+    for sch in (1, 2):
+        with pytest.raises(F.FalconError) as e:
+            F.pipeline_compress(x, block=1024, frame_values=50_000, nstreams=4, out=out, scheduler=sch)
+        assert e.value.status == F.ERR_CAPACITY
+    with pytest.raises(F.FalconError) as e:
+        F.pipeline_compress(x, block=1024, frame_values=50_000, nstreams=4, scheduler=3)
+    assert e.value.status == F.ERR_INVALID
