@@ -40,6 +40,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="falcon", choices=["falcon", "reference"])
     ap.add_argument("--n", type=int, default=N_VALUES, help=argparse.SUPPRESS)
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only the timed kernel steps (every other section off; used by the ncu captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -55,7 +57,12 @@ def parse_args():
     ap.add_argument("--serve-rates", default="1000,2000,5000,10000,20000,50000", help=argparse.SUPPRESS)
     ap.add_argument("--pipeline-values", type=int, default=1 << 31, help=argparse.SUPPRESS)
     ap.add_argument("--batch-series", type=int, default=4096, help=argparse.SUPPRESS)
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.kernels_only:
+        for k in ("no_cpu_baseline", "no_e2e", "no_batched", "no_pipeline", "no_serve", "no_case1", "no_variants",
+                  "no_schedulers", "no_sweeps"):
+            setattr(args, k, True)
+    return args
 
 
 def measured_peaks():
@@ -684,6 +691,23 @@ def bench_serve(args, dev):
                                  "server": serve.run_load(srv, pool, rate=rate, duration=window(rate),
                                                           seed=int(rate))})
             progress(f"server: {rate:g} req/s done")
+        # served results against the oracle: 16 requests of the pool submitted together
+        from oracle import oracle
+        oracle.build()
+        pick = list(range(0, len(pool), max(1, len(pool) // 16)))[:16]
+        futs = [srv.submit(*pool[i]) for i in pick]
+        eq = True
+        for i, f in zip(pick, futs):
+            op, payload = pool[i]
+            got = f.result().numpy()
+            if op == serve.COMPRESS:
+                eq &= got.tobytes() == oracle.compress(payload.numpy(), BLOCK, threads=host_cores())
+            else:
+                want = oracle.decompress(payload.numpy().tobytes(), threads=host_cores())
+                eq &= got.tobytes() == want.tobytes()
+            del got
+        out["oracle_equal"] = bool(eq)
+        out["oracle_check"] = f"{len(pick)} pool requests served together, each against the oracle"
     serve.run_one_at_a_time(pool, rate=500, duration=0.3, seed=99, device=dev)   # warm-up
     for ld in out["loads"]:
         rate = ld["offered_req_s"]
@@ -801,9 +825,6 @@ def bench_pipeline(falcon, synth, torch, dev, n):
             "compress_frac_of_h2d": nbytes / tc / 1e9 / link["h2d"],
             "decompress_frac_of_d2h": nbytes / td / 1e9 / link["d2h"], "setup_s": setup_s}
 
-
-if __name__ == "__main__":
-    main()
 
 
 # ------------------------------------------------------------------------------ more sections
@@ -983,6 +1004,7 @@ def bench_sweeps(falcon, torch, dev, peak):
     fv = 1 << 23
     out_buf = torch.empty(((big + fv - 1) // fv) * falcon.bound(fv, falcon.F64, BLOCK), dtype=torch.uint8,
                           pin_memory=True)
+    back = torch.empty(big, dtype=torch.float64, pin_memory=True)
     for mb in (100, 300, 700, 2048, 8192, 16384):
         m = min(big, mb * (1 << 20) // 8)
         part = h[:m]
@@ -990,8 +1012,9 @@ def bench_sweeps(falcon, torch, dev, peak):
         t0 = time.perf_counter()
         s, fb = falcon.pipeline_compress(part, block=BLOCK, frame_values=fv, out=out_buf)
         tcp = time.perf_counter() - t0
+        falcon.pipeline_decompress(s, fb, out=back)
         t0 = time.perf_counter()
-        falcon.pipeline_decompress(s, fb)
+        falcon.pipeline_decompress(s, fb, out=back)
         tdp = time.perf_counter() - t0
         out["data_size"][f"{mb}MB"] = {"compress_gbs": m * 8 / tcp / 1e9, "decompress_gbs": m * 8 / tdp / 1e9}
     part = h[:1 << 28]
@@ -1001,10 +1024,15 @@ def bench_sweeps(falcon, torch, dev, peak):
         t0 = time.perf_counter()
         s, fb = falcon.pipeline_compress(part, block=BLOCK, frame_values=fvm, out=out_buf)
         tcp = time.perf_counter() - t0
+        falcon.pipeline_decompress(s, fb, out=back)
         t0 = time.perf_counter()
-        falcon.pipeline_decompress(s, fb)
+        falcon.pipeline_decompress(s, fb, out=back)
         tdp = time.perf_counter() - t0
         out["frame_size"][f"{mult}x1025x1024"] = {"compress_gbs": part.numel() * 8 / tcp / 1e9,
                                                   "decompress_gbs": part.numel() * 8 / tdp / 1e9}
-    del h, out_buf
+    del h, out_buf, back
     return out
+
+
+if __name__ == "__main__":
+    main()

@@ -134,30 +134,45 @@ __device__ __forceinline__ typename Traits<F64>::U lane_value(const uint8_t *buf
 
 // Every value of the chunk (the lane's 32 in v, value 1024 of a 1025-value chunk in vx)
 // passes Alg. 2's test at a.  Values past m are +0, which passes.
-// A failing decimal place usually fails on every lane's first value already, so those 32
-// are tested first.
+// Every value of the chunk passes Alg. 2's test at a; the values are re-read from the staging
+// buffer (index >= m: not a value).  A failing decimal place usually fails on every lane's
+// first value already, so those 32 are tested first.
 template <bool F64>
-__device__ __forceinline__ bool all_pass(const typename Traits<F64>::U (&v)[32], typename Traits<F64>::U vx, int a) {
-    if (!__all_sync(kFull, q_test(v[0], a))) return false;
+__device__ __forceinline__ bool all_pass(const uint8_t *buf, int lane, uint32_t m, typename Traits<F64>::U vx,
+                                         int a) {
+    const bool has0 = 32u * lane < m;
+    if (!__all_sync(kFull, !has0 || q_test(lane_value<F64>(buf, lane, 0), a))) return false;
     bool ok = q_test(vx, a);
-#pragma unroll
-    for (int k = 1; k < 32; ++k) ok &= q_test(v[k], a);
+#pragma unroll 4
+    for (int k = 1; k < 32; ++k)
+        if (32u * lane + k < m) ok &= q_test(lane_value<F64>(buf, lane, k), a);
     return __all_sync(kFull, ok);
 }
 
-// FP64: smallest a in [0, atop] at which every value passes, or -1 (Case 2).  For chunks of
-// valid values the predicate is monotone in a (Thm 4 with Thm 3); a single failure at atop
-// means some value is an exception or needs alpha > atop.  The first probe is the previous
-// chunk's alpha (hint), the second the one below it, then bisection; one call site keeps
-// the inlined test once in the code.
-__device__ __forceinline__ int search_alpha64(const uint64_t (&v)[32], uint64_t vx, int atop, int hint) {
-    int lo = 0, hi = atop;                      // the answer, if any, lies in [lo, hi]
+// Smallest a in [0, atop] at which every value passes the round-trip test, or -1 (Case 2).
+// For chunks of valid values the predicate is monotone in a (Thm 4 with Thm 3), and its
+// smallest true point is the largest decimal place of the values; a failure at atop means
+// some value is an exception or needs alpha > atop.  Each lane's first value is tested at
+// atop (a failure settles Case 2), then its own decimal place is found; the warp's maximum
+// is a lower bound, and for most chunks the answer: one all-value test confirms it.
+// Otherwise the answer lies above it (test atop, then bisect).  Out of line, reading the
+// staged values: few chunks get here, and the hot path of the others stays small.
+template <bool F64>
+__device__ __noinline__ int search_alpha(const uint8_t *buf, int lane, uint32_t m, typename Traits<F64>::U vx,
+                                         int atop) {
+    using U = typename Traits<F64>::U;
+    const U v0 = 32u * lane < m ? lane_value<F64>(buf, lane, 0) : (U)0;
+    if (!__all_sync(kFull, q_test(v0, atop))) return -1;
+    int a0 = 0;
+#pragma unroll 1
+    while (a0 < atop && !q_test(v0, a0)) ++a0;
+    const int lb = (int)__reduce_max_sync(kFull, (uint32_t)a0);
+    int lo = lb, hi = atop;                     // the answer, if any, lies in [lo, hi]
     bool hi_ok = false;                         // all_pass(hi) is known to hold
-    int a = (hint >= 0 && hint < atop) ? hint : atop;
-    bool first_ok = false, probed_below = false;
+    int a = lb;
 #pragma unroll 1
     for (;;) {
-        const bool ok = all_pass<true>(v, vx, a);
+        const bool ok = all_pass<F64>(buf, lane, m, vx, a);
         if (ok) {
             hi = a;
             hi_ok = true;
@@ -166,24 +181,18 @@ __device__ __forceinline__ int search_alpha64(const uint64_t (&v)[32], uint64_t 
             lo = a + 1;
         }
         if (hi_ok && lo >= hi) return hi;
-        if (!hi_ok) {
-            a = atop;                           // the hint failed: is Case 1 possible at all?
-        } else if (ok && !probed_below && !first_ok) {
-            first_ok = true;
-            probed_below = true;
-            a = hi - 1;                         // most chunks keep their neighbour's alpha
-        } else {
-            a = (lo + hi) >> 1;                 // lo <= a < hi
-        }
-        first_ok = true;
+        a = hi_ok ? ((lo + hi) >> 1) : atop;    // lo <= a < hi once atop has passed
     }
 }
 
 // FP32: alpha_max = max over values of Alg. 2's decimal place (the first a with eps <= mu,
 // accepted only if the round trip holds there), restricted to [0, atop], then the R6 check
 // that every value round-trips at alpha_max; -1 means Case 2.  The values are tested a
-// decimal place at a time, all 32 of a lane together (no divergent per-value loops).
-__device__ __forceinline__ int alpha32(const uint32_t (&v)[32], uint32_t vx, bool has_vx, int atop) {
+// decimal place at a time, all of a lane's together (no divergent per-value loops).
+__device__ __noinline__ int alpha32(const uint8_t *buf, int lane, uint32_t m, uint32_t vx, bool has_vx, int atop) {
+    uint32_t v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = 32u * lane + k < m ? lane_value<false>(buf, lane, k) : 0u;
     uint32_t open = 0xFFFFFFFFu;                // values of this lane still without a decimal place
     bool open_x = has_vx;
     bool bad = false;
@@ -209,7 +218,7 @@ __device__ __forceinline__ int alpha32(const uint32_t (&v)[32], uint32_t vx, boo
     }
     if (__any_sync(kFull, bad || open != 0u || open_x)) return -1;
     amax = (int)__reduce_max_sync(kFull, (uint32_t)amax);
-    return all_pass<false>(v, vx, amax) ? amax : -1;
+    return all_pass<false>(buf, lane, m, vx, amax) ? amax : -1;
 }
 
 // Fal._Elf's decimal place of one value (Sec. 1's trial and error, ablation of Sec. 5.4.2):
@@ -241,22 +250,25 @@ __device__ __forceinline__ int elf_dp(uint32_t u) {
 }
 
 // Fal._Elf: alpha_max = the largest of the values' Elf decimal places, then Eq. 4's bounds and
-// the R6 round trip at alpha_max, as for Falcon; -1 means Case 2.
+// the R6 round trip at alpha_max, as for Falcon; -1 means Case 2.  Out of line (an ablation).
 template <bool F64>
-__device__ int alpha_elf(const typename Traits<F64>::U (&v)[32], typename Traits<F64>::U vx, bool has_vx, int e_max) {
+__device__ __noinline__ int alpha_elf(const uint8_t *buf, int lane, uint32_t m, typename Traits<F64>::U vx,
+                                      bool has_vx, int e_max) {
     using T = Traits<F64>;
     int amax = has_vx ? elf_dp(vx) : 0;
     bool bad = amax < 0;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {              // values past m are +0: decimal place 0
-        const int a = elf_dp(v[k]);
-        bad |= a < 0;
-        amax = a > amax ? a : amax;
+#pragma unroll 1
+    for (int k = 0; k < 32; ++k) {
+        if (32u * lane + k < m) {
+            const int a = elf_dp(lane_value<F64>(buf, lane, k));
+            bad |= a < 0;
+            amax = a > amax ? a : amax;
+        }
     }
     if (__any_sync(kFull, bad)) return -1;
     amax = (int)__reduce_max_sync(kFull, (uint32_t)amax);
     if (amax > T::A_MAX || amax + e_max + 1 > T::B_MAX) return -1;
-    return all_pass<F64>(v, vx, amax) ? amax : -1;
+    return all_pass<F64>(buf, lane, m, vx, amax) ? amax : -1;
 }
 
 __device__ __forceinline__ void issue_chunk(const Job *jobs, int njobs, const Job &single, uint64_t t,
@@ -326,7 +338,7 @@ __device__ __forceinline__ uint32_t spread_nibble(uint32_t n) { return (n * 0x00
 // staged values are no longer read (after the Case decision).
 template <bool F64, class Next>
 __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, uint8_t *scratch, int lane,
-                              int &hint, Next &&next) {
+                              Next &&next) {
     using T = Traits<F64>;
     using U = typename T::U;
     constexpr U ABS = F64 ? (U)0x7FFFFFFFFFFFFFFFull : (U)0x7FFFFFFFu;
@@ -387,7 +399,7 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
             const int e_max = floor_log10(vmax);
             const int atop = min(T::A_MAX, T::B_MAX - 1 - e_max);
             if (job.variant == kVariantElf) {
-                alpha = alpha_elf<F64>(v, vx, m > 1024u && lane == 31, e_max);
+                alpha = alpha_elf<F64>(buf, lane, m, vx, m > 1024u && lane == 31, e_max);
             } else if (atop >= 0) {
                 // quick rejection: Alg. 2 on the largest magnitude first.  The test reads
                 // only |v|, so it runs on vmax itself, the same in every lane.
@@ -395,14 +407,20 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
                 if constexpr (F64) fail = !q_test(vmax, atop);
                 else fail = first_pass_f32(vmax, atop) < 0;
                 if (!fail) {
-                    if constexpr (F64) alpha = search_alpha64(v, vx, atop, hint);
-                    else alpha = alpha32(v, vx, m > 1024u && lane == 31, atop);
+                    alpha = search_alpha<F64>(buf, lane, m, vx, atop);
+                    // FP32 (R14): with beta <= 6 no value can pass eps <= mu below its decimal
+                    // place (the distance to the nearest integer exceeds 1.5 * 2^-23 |x|), so
+                    // Alg. 2 value by value gives the same alpha_max; at beta_hat = 7 an early
+                    // pass is possible and the values go through Alg. 2 one by one.
+                    if constexpr (!F64) {
+                        if (alpha >= 0 && alpha + e_max + 1 == T::B_MAX)
+                            alpha = alpha32(buf, lane, m, vx, m > 1024u && lane == 31, atop);
+                    }
                 }
             }
             if (alpha >= 0) beta_hat = alpha + e_max + 1;
         }
     }
-    hint = alpha;
     __syncwarp();
     next();                                     // the staged values have been read
 
@@ -639,8 +657,14 @@ __device__ __forceinline__ const Job &job_of(const Job *jobs, int njobs, const J
 
 }  // namespace
 
+// The hot kernels come in three forms by dtype: kDt = 0 (every job FP64), 1 (every job FP32)
+// or 2 (either, per job: batches and the server).  A single-dtype form carries half the code,
+// which the instruction caches notice.
+constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2;
+
 // Launch 1: analysis of every chunk (fixed stride per warp; the next chunk is copied into
 // the warp's one value buffer while the current one is finished).
+template <int kDt>
 __global__ void __launch_bounds__(kThreads, 4)
 analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -654,7 +678,6 @@ analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t tot
     const uint64_t gw = (uint64_t)blockIdx.x * kWarpsPerCta + warp;
     const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
     if (gw >= total_chunks) return;
-    int hint64 = -1, hint32 = -1;
     issue_chunk(jobs, njobs, s_single, gw, wbase, lane);
     cp_async_commit();
     for (uint64_t t = gw; t < total_chunks; t += nw) {
@@ -667,8 +690,10 @@ analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t tot
         };
         const Job &job = job_of(jobs, njobs, s_single, t);
         const uint64_t c = t - job.chunk_begin;
-        if (job.dtype == 0) analyse_chunk<true>(job, c, wbase, scratch, lane, hint64, next);
-        else analyse_chunk<false>(job, c, wbase, scratch, lane, hint32, next);
+        if constexpr (kDt == kDtF64) analyse_chunk<true>(job, c, wbase, scratch, lane, next);
+        else if constexpr (kDt == kDtF32) analyse_chunk<false>(job, c, wbase, scratch, lane, next);
+        else if (job.dtype == 0) analyse_chunk<true>(job, c, wbase, scratch, lane, next);
+        else analyse_chunk<false>(job, c, wbase, scratch, lane, next);
         __syncwarp();
     }
     cp_async_wait_none();
@@ -708,7 +733,7 @@ __device__ __forceinline__ EmitInfo load_info(const Job &job, uint64_t c, int la
 }
 
 // Launch 3: the records (fixed stride per warp; the next chunk's values are prefetched into L2).
-template <bool kWide>
+template <bool kWide, int kDt>
 __global__ void __launch_bounds__(kThreads, 4)
 emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -737,7 +762,9 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
         const Job &job = job_of(jobs, njobs, s_single, t);
         const uint64_t c = t - job.chunk_begin;
         const uint64_t rel = resolve_pos(info.pos);
-        if (job.dtype == 0) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
+        if constexpr (kDt == kDtF64) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
+        else if constexpr (kDt == kDtF32) emit_chunk<false, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
+        else if (job.dtype == 0) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
         else emit_chunk<false, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
         __syncwarp();
         info = next;
@@ -757,7 +784,22 @@ int persistent_grid(K kernel, int smem_bytes, uint64_t total_chunks) {
 }
 }  // namespace
 
-int compress_grid(uint64_t total_chunks) { return persistent_grid(emit_kernel<false>, kEmitCtaSmem<false>, total_chunks); }
+int compress_grid(uint64_t total_chunks) {
+    return persistent_grid(emit_kernel<false, kDtMixed>, kEmitCtaSmem<false>, total_chunks);
+}
+
+namespace {
+template <int kDt>
+void launch_analyse(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, cudaStream_t stream) {
+    const int g = persistent_grid(analyse_kernel<kDt>, kAnalyseCtaSmem, total_chunks);
+    analyse_kernel<kDt><<<g, kThreads, kAnalyseCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
+}
+template <bool kWide, int kDt>
+void launch_emit(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, cudaStream_t stream) {
+    const int g = persistent_grid(emit_kernel<kWide, kDt>, kEmitCtaSmem<kWide>, total_chunks);
+    emit_kernel<kWide, kDt><<<g, kThreads, kEmitCtaSmem<kWide>, stream>>>(d_jobs, njobs, single, total_chunks);
+}
+}  // namespace
 
 namespace {
 // Resident CTAs per SM of a persistent kernel, looked up once per (kernel, device) under a
@@ -796,19 +838,19 @@ cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single, uin
     (void)ctl;
     // the every-row-sparse ablation writes records larger than the plane slots hold
     const bool wide = d_jobs == nullptr && single.variant == kVariantSparse;
+    const int kind = d_jobs != nullptr ? kDtMixed : (single.dtype == 0 ? kDtF64 : kDtF32);
     if (total_chunks > 0) {
-        const int g1 = persistent_grid(analyse_kernel, kAnalyseCtaSmem, total_chunks);
-        analyse_kernel<<<g1, kThreads, kAnalyseCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
+        if (kind == kDtF64) launch_analyse<kDtF64>(d_jobs, njobs, single, total_chunks, stream);
+        else if (kind == kDtF32) launch_analyse<kDtF32>(d_jobs, njobs, single, total_chunks, stream);
+        else launch_analyse<kDtMixed>(d_jobs, njobs, single, total_chunks, stream);
     }
     compress_offsets_kernel<<<(d_jobs != nullptr) ? njobs : 1, 1024, 0, stream>>>(d_jobs, single);
     if (total_chunks > 0) {
-        if (wide) {
-            const int g3 = persistent_grid(emit_kernel<true>, kEmitCtaSmem<true>, total_chunks);
-            emit_kernel<true><<<g3, kThreads, kEmitCtaSmem<true>, stream>>>(d_jobs, njobs, single, total_chunks);
-        } else {
-            const int g3 = persistent_grid(emit_kernel<false>, kEmitCtaSmem<false>, total_chunks);
-            emit_kernel<false><<<g3, kThreads, kEmitCtaSmem<false>, stream>>>(d_jobs, njobs, single, total_chunks);
-        }
+        if (wide && kind == kDtF64) launch_emit<true, kDtF64>(d_jobs, njobs, single, total_chunks, stream);
+        else if (wide) launch_emit<true, kDtF32>(d_jobs, njobs, single, total_chunks, stream);
+        else if (kind == kDtF64) launch_emit<false, kDtF64>(d_jobs, njobs, single, total_chunks, stream);
+        else if (kind == kDtF32) launch_emit<false, kDtF32>(d_jobs, njobs, single, total_chunks, stream);
+        else launch_emit<false, kDtMixed>(d_jobs, njobs, single, total_chunks, stream);
     }
     return cudaGetLastError();
 }

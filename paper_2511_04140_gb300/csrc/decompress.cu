@@ -380,6 +380,10 @@ offsets_kernel(const Job *__restrict__ jobs, Job single) {
     (void)tile_prefix(reinterpret_cast<const uint32_t *>(job.in + 32), job.nchunks, job.flags, warp_sums);
 }
 
+// Forms by dtype: kDt = 0 (every job FP64), 1 (every job FP32), 2 (either, per job).
+constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2;
+
+template <int kDt>
 __global__ void __launch_bounds__(kThreads, 3)
 decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -421,7 +425,9 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
             cp_async_commit();
         };
         const Job &job = job_of(jobs, njobs, s_single, t);
-        if (job.dtype == 0) decode_chunk<true>(job, lc, okc, wbase, pbuf, lane, next);
+        if constexpr (kDt == kDtF64) decode_chunk<true>(job, lc, okc, wbase, pbuf, lane, next);
+        else if constexpr (kDt == kDtF32) decode_chunk<false>(job, lc, okc, wbase, pbuf, lane, next);
+        else if (job.dtype == 0) decode_chunk<true>(job, lc, okc, wbase, pbuf, lane, next);
         else decode_chunk<false>(job, lc, okc, wbase, pbuf, lane, next);
         lc = ln;
         okc = okn;
@@ -433,15 +439,26 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
 constexpr int kDecompressCtaSmem = kWarpsPerCta * kWarpBytes;
 
 int decompress_grid(uint64_t total_chunks) {
-    return persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel), kDecompressCtaSmem,
+    return persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDtMixed>), kDecompressCtaSmem,
                                 g_ctas_per_sm[1], total_chunks);
 }
+
+namespace {
+template <int kDt>
+void launch_decode(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
+                   cudaStream_t stream) {
+    const int grid = persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDt>), kDecompressCtaSmem,
+                                          g_ctas_per_sm[1], total_chunks);
+    decompress_kernel<kDt><<<grid, kThreads, kDecompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+}
+}  // namespace
 
 cudaError_t launch_decompress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,
                               Control *ctl, cudaStream_t stream) {
     offsets_kernel<<<(d_jobs != nullptr) ? njobs : 1, 1024, 0, stream>>>(d_jobs, single);
-    const int grid = decompress_grid(total_chunks);
-    decompress_kernel<<<grid, kThreads, kDecompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+    if (d_jobs != nullptr) launch_decode<kDtMixed>(d_jobs, njobs, single, total_chunks, ctl, stream);
+    else if (single.dtype == 0) launch_decode<kDtF64>(d_jobs, njobs, single, total_chunks, ctl, stream);
+    else launch_decode<kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
     return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built libfalcon")
+    config.addinivalue_line("markers", "slow: takes about a minute or more (deselect with -m 'not slow')")
 
 
 @pytest.fixture(scope="session")
