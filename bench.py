@@ -684,6 +684,12 @@ def bench_serve(args, dev):
                        f"50/50 compress/decompress, Poisson arrivals; {args.serve_seconds:g} s per load up to "
                        f"5k req/s, {args.serve_seconds_saturated:g} s above (saturated)",
            "budget_bytes": 64 << 30, "loads": []}
+    # the client's Python collector could pause every thread for tens of ms inside a window
+    # (this process holds the other sections' objects): collect once, then keep it off while
+    # the loads run, for the server and the one-at-a-time baseline alike
+    import gc
+    gc.collect()
+    gc.disable()
     with serve.Server(budget_bytes=64 << 30, host_budget_bytes=16 << 30, device=dev) as srv:
         serve.run_load(srv, pool, rate=500, duration=0.3, seed=99)              # warm-up
         for rate in rates:
@@ -715,6 +721,8 @@ def bench_serve(args, dev):
                                                       device=dev)
         ld["gbs_vs_one_at_a_time"] = ld["server"]["gbs"] / ld["one_at_a_time"]["gbs"]
         progress(f"one at a time: {rate:g} req/s done")
+    gc.enable()
+    out["client"] = "Python garbage collection off during the timed windows (both forms)"
     return out
 
 

@@ -39,16 +39,26 @@ struct Slot {
     uint8_t *h_stage = nullptr;       // pinned, pre-allocation scheduler only
     size_t stage_bytes = 0;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t up = nullptr;         // the frame's upload is done
     SlotState state = kIdle;
     uint64_t frame = 0;
 };
 
 struct SlotSet {
     std::vector<Slot> slots;
+    // one stream for every frame's kernels, in launch order: compression is an order of
+    // magnitude faster than the host link, and frames whose kernels ran side by side on
+    // several streams could finish out of order, holding up the in-order placement
+    cudaStream_t compute = nullptr;
     ~SlotSet() {
+        if (compute) {
+            cudaStreamSynchronize(compute);
+            cudaStreamDestroy(compute);
+        }
         for (Slot &s : slots) {
             if (s.stream) cudaStreamSynchronize(s.stream);
             if (s.ev) cudaEventDestroy(s.ev);
+            if (s.up) cudaEventDestroy(s.up);
             if (s.stream) cudaStreamDestroy(s.stream);
             cudaFree(s.d_in);
             cudaFree(s.d_out);
@@ -59,10 +69,12 @@ struct SlotSet {
         }
     }
     int init(int n, size_t in_bytes, size_t out_bytes, size_t ws_bytes) {
+        if (cudaStreamCreateWithFlags(&compute, cudaStreamNonBlocking) != cudaSuccess) return FALCON_ERR_CUDA;
         slots.resize((size_t)n);
         for (Slot &s : slots) {
             if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) return FALCON_ERR_CUDA;
             if (cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess) return FALCON_ERR_CUDA;
+            if (cudaEventCreateWithFlags(&s.up, cudaEventDisableTiming) != cudaSuccess) return FALCON_ERR_CUDA;
             if (cudaMalloc(&s.d_in, in_bytes ? in_bytes : 16) != cudaSuccess) return FALCON_ERR_CUDA;
             if (cudaMalloc(&s.d_out, out_bytes ? out_bytes : 16) != cudaSuccess) return FALCON_ERR_CUDA;
             if (cudaMalloc(&s.d_ws, ws_bytes) != cudaSuccess) return FALCON_ERR_CUDA;
@@ -175,16 +187,26 @@ int falcon_pipeline_compress_with(const void *h_in, uint64_t n, int dtype, uint3
     auto launch = [&](Slot &sl, uint64_t f) -> int {
         const uint64_t first = f * frame_values;
         const uint64_t m = (n - first) < frame_values ? (n - first) : frame_values;
+        // upload on the slot's stream; kernels and the result words on the shared compute
+        // stream, in launch order; the whole output slot (pre-allocation) on the slot's stream
         if (cudaMemcpyAsync(sl.d_in, in8 + first * s, m * s, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
             return FALCON_ERR_CUDA;
+        if (cudaEventRecord(sl.up, sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+        if (cudaStreamWaitEvent(set.compute, sl.up, 0) != cudaSuccess) return FALCON_ERR_CUDA;
         const int r = falcon_compress_async(sl.d_in, m, dtype, block_size, sl.d_out, fbound, sl.d_ws, ws_bytes,
-                                            sl.d_res, sl.stream);
+                                            sl.d_res, set.compute);
         if (r) return r;
-        if (cudaMemcpyAsync(sl.h_res, sl.d_res, 16, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+        if (cudaMemcpyAsync(sl.h_res, sl.d_res, 16, cudaMemcpyDeviceToHost, set.compute) != cudaSuccess)
             return FALCON_ERR_CUDA;
-        if (prealloc && cudaMemcpyAsync(sl.h_stage, sl.d_out, fbound, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+        if (prealloc) {
+            if (cudaEventRecord(sl.up, set.compute) != cudaSuccess) return FALCON_ERR_CUDA;
+            if (cudaStreamWaitEvent(sl.stream, sl.up, 0) != cudaSuccess) return FALCON_ERR_CUDA;
+            if (cudaMemcpyAsync(sl.h_stage, sl.d_out, fbound, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+                return FALCON_ERR_CUDA;
+            if (cudaEventRecord(sl.ev, sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+        } else if (cudaEventRecord(sl.ev, set.compute) != cudaSuccess) {
             return FALCON_ERR_CUDA;
-        if (cudaEventRecord(sl.ev, sl.stream) != cudaSuccess) return FALCON_ERR_CUDA;
+        }
         sl.frame = f;
         sl.state = kMPend;
         return FALCON_OK;
@@ -256,6 +278,7 @@ int falcon_pipeline_compress_with(const void *h_in, uint64_t n, int dtype, uint3
             if (!progress) std::this_thread::yield();
         }
     }
+    if (cudaStreamSynchronize(set.compute) != cudaSuccess) return FALCON_ERR_CUDA;
     for (uint64_t i = 0; i < ns; ++i)
         if (cudaStreamSynchronize(set.slots[i].stream) != cudaSuccess) return FALCON_ERR_CUDA;
     if (status != FALCON_OK) return status;

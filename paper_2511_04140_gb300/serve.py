@@ -221,11 +221,24 @@ def _summary(lat, nbytes, wall, n):
 
 
 def run_one_at_a_time(pool, rate: float, duration: float, seed: int = 0, device="cuda", block: int = 1024) -> dict:
-    """The same arrivals served strictly one request at a time (upload, one kernel launch,
-    download, next): the queue-only baseline."""
+    """The same arrivals served strictly one request at a time (upload, one compress or
+    decompress call, download, next): the queue-only baseline.  Its device and page-locked
+    host buffers are allocated once, for the largest request, and reused, as the server's
+    arenas are."""
     dev = torch.device(device)
     arr = _arrivals(rate, duration, len(pool), seed)
     stream = torch.cuda.Stream(dev)
+    in_max = max(p.numel() * p.element_size() for _, p in pool)
+    out_max = 0
+    for op, p in pool:
+        if op == COMPRESS:
+            out_max = max(out_max, falcon.bound(p.numel(), falcon._dtype_code(p), block))
+        else:
+            n, code, _, _ = falcon.stream_info(p[:falcon.HEADER_BYTES].numpy().tobytes())
+            out_max = max(out_max, n * (8 if code == falcon.F64 else 4))
+    d_in = torch.empty((in_max + 15) // 16 * 16, dtype=torch.uint8, device=dev)
+    d_out = torch.empty(max(out_max, 32) // 8 * 8 + 8, dtype=torch.uint8, device=dev)
+    h_out = torch.empty(max(out_max, 32), dtype=torch.uint8, pin_memory=True)
     t0 = time.perf_counter()
     lat, nbytes = [], 0
     with torch.cuda.stream(stream):
@@ -234,19 +247,20 @@ def run_one_at_a_time(pool, rate: float, duration: float, seed: int = 0, device=
             if t > now:
                 time.sleep(t - now)
             op, payload = pool[i]
+            nb = payload.numel() * payload.element_size()
+            d_in[:nb].copy_(payload.view(torch.uint8), non_blocking=True)
             if op == COMPRESS:
-                d = payload.to(dev, non_blocking=True)
-                s = falcon.compress(d, block, stream=stream)
-                out = torch.empty(s.numel(), dtype=torch.uint8, pin_memory=True)
+                x = d_in[:nb].view(payload.dtype)
+                s = falcon.compress(x, block, out=d_out, stream=stream)
+                out = h_out[:s.numel()]
                 out.copy_(s)
             else:
-                d = torch.empty(((payload.numel() + 15) // 16) * 16, dtype=torch.uint8, device=dev)
-                d[:payload.numel()].copy_(payload, non_blocking=True)
-                y = falcon.decompress(d[:payload.numel()], stream=stream)
-                out = torch.empty(y.numel(), dtype=y.dtype, pin_memory=True)
-                out.copy_(y)
+                y = falcon.decompress(d_in[:nb], out=d_out.view(torch.float64 if payload[5] == falcon.F64
+                                                                else torch.float32), stream=stream)
+                out = h_out[:y.numel() * y.element_size()]
+                out.copy_(y.view(torch.uint8))
             lat.append(time.perf_counter() - t0 - t)
-            nbytes += _bytes_of(op, payload, out)
+            nbytes += nb if op == COMPRESS else out.numel()
     wall = time.perf_counter() - t0
     return _summary(lat, nbytes, wall, len(arr))
 
