@@ -40,6 +40,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="falcon", choices=["falcon", "reference"])
     ap.add_argument("--n", type=int, default=N_VALUES, help=argparse.SUPPRESS)
+    ap.add_argument("--section", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--kernels-only", action="store_true",
                     help="only the timed kernel steps (every other section off; used by the ncu captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -386,6 +387,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.section:
+        return section_main(args)
 
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -521,23 +524,15 @@ def main():
     if rank == 0 and not args.no_batched:
         progress("batched launch")
         line["batched"] = bench_batched(falcon, synth, torch, dev, args.batch_series)
-    if rank == 0 and not args.no_pipeline:
-        release_caches(torch)
-        progress("host pipeline")
-        line["pipeline"] = bench_pipeline(falcon, synth, torch, dev, args.pipeline_values)
-        release_caches(torch)
-    if rank == 0 and not args.no_schedulers:
-        progress("pipeline schedulers")
-        line["schedulers"] = bench_schedulers(falcon, torch, dev)
-        release_caches(torch)
-    if rank == 0 and not args.no_sweeps:
-        progress("parameter sweeps")
-        line["sweeps"] = bench_sweeps(falcon, torch, dev, peak)
-        release_caches(torch)
-    if rank == 0 and not args.no_serve:
-        progress("server")
-        line["serve"] = bench_serve(args, dev)
-        release_caches(torch)
+    # the host-link sections run each in a fresh process: in one long process, the state the
+    # earlier sections leave behind made host <-> device copies of later ones erratic
+    # (measured: the 16 GiB pipeline at 167-177 GB/s alone, 52-69 GB/s after the batched
+    # section), and a user runs each such workload on its own
+    for name, skip in (("pipeline", args.no_pipeline), ("schedulers", args.no_schedulers),
+                       ("sweeps", args.no_sweeps), ("serve", args.no_serve)):
+        if rank == 0 and not skip:
+            progress(name + " (own process)")
+            line[name] = run_section(name, args)
     if rank == 0 and not args.no_cpu_baseline:
         progress("cpu baseline")
         line["cpu_baseline"] = cpu_baseline(host)
@@ -550,6 +545,47 @@ def main():
     if failed:
         sys.stderr.write("bench: bit-exactness check failed in " + ", ".join(failed) + "\n")
         sys.exit(1)
+
+
+def run_section(name: str, args) -> dict:
+    """Runs one bench section in a fresh Python process on this process's GPU and returns
+    its result (the last JSON line it prints)."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--section", name,
+           "--serve-seconds", str(args.serve_seconds), "--serve-seconds-saturated", str(args.serve_seconds_saturated),
+           "--serve-pool", str(args.serve_pool), "--serve-rates", args.serve_rates,
+           "--pipeline-values", str(args.pipeline_values)]
+    env = dict(os.environ)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    import torch
+    vis, idx = os.environ.get("CUDA_VISIBLE_DEVICES"), torch.cuda.current_device()
+    env["CUDA_VISIBLE_DEVICES"] = vis.split(",")[idx] if vis else str(idx)      # the same GPU, as cuda:0
+    res = subprocess.run(cmd, stdout=subprocess.PIPE, text=True, env=env)
+    if res.returncode != 0:
+        raise RuntimeError(f"bench section {name} failed (rc {res.returncode})")
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def section_main(args):
+    """One section, alone in this process (see run_section)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    from paper_2511_04140_gb300 import build as fbuild
+    fbuild.build()
+    from paper_2511_04140_gb300 import falcon, synth
+    peak, _ = measured_peaks()
+    if args.section == "pipeline":
+        out = bench_pipeline(falcon, synth, torch, dev, args.pipeline_values)
+    elif args.section == "schedulers":
+        out = bench_schedulers(falcon, torch, dev)
+    elif args.section == "sweeps":
+        out = bench_sweeps(falcon, torch, dev, peak)
+    elif args.section == "serve":
+        out = bench_serve(args, dev)
+    else:
+        raise SystemExit(f"unknown section {args.section}")
+    print(json.dumps(out), flush=True)
 
 
 def failed_checks(obj, path="line"):
@@ -666,6 +702,7 @@ def bench_batched(falcon, synth, torch, dev, count):
     comp.close()
     dec.close()
     falcon.set_launch_config(0, 0)
+    falcon.set_cta_warps(4, 4)
     return out
 
 

@@ -361,6 +361,11 @@ int falcon_server_destroy(falcon_server *server);
  * (0 = as many as fit).  Does not change any output byte; used by the autotuner. */
 int falcon_set_launch_config(int compress_ctas_per_sm, int decompress_ctas_per_sm);
 
+/* Threads per CTA of the persistent kernels, in warps (each warp works on its own chunks):
+ * 1..16 for compression, 1..12 for decompression (default 4 and 4).  Does not change any
+ * output byte; used by the autotuner.  FALCON_ERR_INVALID outside those ranges. */
+int falcon_set_cta_warps(int compress_warps, int decompress_warps);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,6 +15,7 @@ void falcon_noalloc_release();
 
 namespace falcon {
 int g_ctas_per_sm[2] = {0, 0};
+int g_cta_warps[2] = {kWarpsPerCta, kWarpsPerCta};
 }
 
 namespace {
@@ -459,6 +460,15 @@ int falcon_batch_launch(void *d_workspace, void *stream) {
 int falcon_batch_forget(void *d_workspace) {
     std::lock_guard<std::mutex> lk(g_plan_mu);
     g_plans.erase((uintptr_t)d_workspace);
+    return FALCON_OK;
+}
+
+int falcon_set_cta_warps(int compress_warps, int decompress_warps) {
+    if (compress_warps < 1 || compress_warps > kMaxCompressWarps || decompress_warps < 1 ||
+        decompress_warps > kMaxDecompressWarps)
+        return FALCON_ERR_INVALID;
+    g_cta_warps[0] = compress_warps;
+    g_cta_warps[1] = decompress_warps;
     return FALCON_OK;
 }
 

@@ -24,6 +24,7 @@
 // the analysis recomputed by the emit launch costs less.
 #include <map>
 #include <mutex>
+#include <tuple>
 
 #include "falcon_device.cuh"
 
@@ -665,7 +666,7 @@ constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2;
 // Launch 1: analysis of every chunk (fixed stride per warp; the next chunk is copied into
 // the warp's one value buffer while the current one is finished).
 template <int kDt>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(32 * kMaxCompressWarps, 1)
 analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -675,8 +676,8 @@ analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t tot
     __shared__ Job s_single;                      // the single job, read from shared memory
     if (threadIdx.x == 0) s_single = single;
     __syncthreads();
-    const uint64_t gw = (uint64_t)blockIdx.x * kWarpsPerCta + warp;
-    const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
+    const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
     if (gw >= total_chunks) return;
     issue_chunk(jobs, njobs, s_single, gw, wbase, lane);
     cp_async_commit();
@@ -734,7 +735,7 @@ __device__ __forceinline__ EmitInfo load_info(const Job &job, uint64_t c, int la
 
 // Launch 3: the records (fixed stride per warp; the next chunk's values are prefetched into L2).
 template <bool kWide, int kDt>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(32 * kMaxCompressWarps, 1)
 emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -743,8 +744,8 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
     __shared__ Job s_single;
     if (threadIdx.x == 0) s_single = single;
     __syncthreads();
-    const uint64_t gw = (uint64_t)blockIdx.x * kWarpsPerCta + warp;
-    const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
+    const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
     if (gw >= total_chunks) return;
     EmitInfo info;
     {
@@ -772,65 +773,62 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
     if (lane == 0) bulk_wait();
 }
 
-template <bool kWide> constexpr int kEmitCtaSmem = kWarpsPerCta * EmitLayout<kWide>::kBytes;
-constexpr int kAnalyseCtaSmem = kWarpsPerCta * kAnalyseWarpBytes;
-
 namespace {
-int persistent_grid_of(const void *kernel, int smem_bytes, int lim, uint64_t total_chunks);
+int persistent_grid_of(const void *kernel, int warps, int smem_bytes, int lim, uint64_t total_chunks);
 
-template <typename K>
-int persistent_grid(K kernel, int smem_bytes, uint64_t total_chunks) {
-    return persistent_grid_of(reinterpret_cast<const void *>(kernel), smem_bytes, g_ctas_per_sm[0], total_chunks);
-}
-}  // namespace
-
-int compress_grid(uint64_t total_chunks) {
-    return persistent_grid(emit_kernel<false, kDtMixed>, kEmitCtaSmem<false>, total_chunks);
-}
-
-namespace {
 template <int kDt>
 void launch_analyse(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, cudaStream_t stream) {
-    const int g = persistent_grid(analyse_kernel<kDt>, kAnalyseCtaSmem, total_chunks);
-    analyse_kernel<kDt><<<g, kThreads, kAnalyseCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks);
+    const int w = g_cta_warps[0], smem = w * kAnalyseWarpBytes;
+    const int g = persistent_grid_of(reinterpret_cast<const void *>(analyse_kernel<kDt>), w, smem, g_ctas_per_sm[0],
+                                     total_chunks);
+    analyse_kernel<kDt><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks);
 }
 template <bool kWide, int kDt>
 void launch_emit(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, cudaStream_t stream) {
-    const int g = persistent_grid(emit_kernel<kWide, kDt>, kEmitCtaSmem<kWide>, total_chunks);
-    emit_kernel<kWide, kDt><<<g, kThreads, kEmitCtaSmem<kWide>, stream>>>(d_jobs, njobs, single, total_chunks);
+    const int w = g_cta_warps[0], smem = w * EmitLayout<kWide>::kBytes;
+    const int g = persistent_grid_of(reinterpret_cast<const void *>(emit_kernel<kWide, kDt>), w, smem,
+                                     g_ctas_per_sm[0], total_chunks);
+    emit_kernel<kWide, kDt><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks);
 }
-}  // namespace
 
-namespace {
-// Resident CTAs per SM of a persistent kernel, looked up once per (kernel, device) under a
-// lock (the server and the pipeline launch from several host threads).
+// Resident CTAs per SM of a persistent kernel at one CTA shape, looked up once per (kernel,
+// device, shape) under a lock (the server and the pipeline launch from several host threads).
 std::mutex g_occ_mu;
-std::map<std::pair<const void *, int>, std::pair<int, int>> g_occ;   // -> (CTAs per SM, SMs)
+std::map<std::tuple<const void *, int, int, int>, std::pair<int, int>> g_occ;   // -> (CTAs per SM, SMs)
 
-int persistent_grid_of(const void *kernel, int smem_bytes, int lim, uint64_t total_chunks) {
+int persistent_grid_of(const void *kernel, int warps, int smem_bytes, int lim, uint64_t total_chunks) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::pair<int, int> oc;
     {
         std::lock_guard<std::mutex> lk(g_occ_mu);
-        auto it = g_occ.find({kernel, dev});
+        const auto key = std::make_tuple(kernel, dev, warps, smem_bytes);
+        auto it = g_occ.find(key);
         if (it == g_occ.end()) {
             cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
             int sms = 0, occ = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, smem_bytes);
-            it = g_occ.emplace(std::make_pair(kernel, dev), std::make_pair(occ > 0 ? occ : 1, sms > 0 ? sms : 1)).first;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 32 * warps, smem_bytes);
+            it = g_occ.emplace(key, std::make_pair(occ > 0 ? occ : 1, sms > 0 ? sms : 1)).first;
+        } else {
+            cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
         }
         oc = it->second;
     }
     const int cached = oc.second * ((lim > 0 && lim < oc.first) ? lim : oc.first);
-    const uint64_t need = (total_chunks + kWarpsPerCta - 1) / kWarpsPerCta;
+    const uint64_t need = (total_chunks + (uint64_t)warps - 1) / (uint64_t)warps;
     return (int)(need < (uint64_t)cached ? (need > 0 ? need : 1) : (uint64_t)cached);
 }
 }  // namespace
 
-int persistent_grid_size(const void *kernel, int smem_bytes, int lim, uint64_t total_chunks) {
-    return persistent_grid_of(kernel, smem_bytes, lim, total_chunks);
+int persistent_grid_size(const void *kernel, int warps, int smem_bytes, int lim, uint64_t total_chunks) {
+    return persistent_grid_of(kernel, warps, smem_bytes, lim, total_chunks);
+}
+
+int compress_grid(uint64_t total_chunks) {
+    const int w = g_cta_warps[0];
+    return persistent_grid_of(reinterpret_cast<const void *>(emit_kernel<false, kDtMixed>), w,
+                              w * EmitLayout<false>::kBytes, g_ctas_per_sm[0], total_chunks);
 }
 
 cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,

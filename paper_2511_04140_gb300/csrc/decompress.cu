@@ -384,7 +384,7 @@ offsets_kernel(const Job *__restrict__ jobs, Job single) {
 constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2;
 
 template <int kDt>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(32 * kMaxDecompressWarps, 1)
 decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -395,8 +395,8 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
     if (threadIdx.x == 0) s_single = single;
     init_expand_sel();
     __syncthreads();
-    const uint64_t gw = (uint64_t)blockIdx.x * kWarpsPerCta + warp;
-    const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerCta;
+    const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
     (void)ctl;
     for (uint64_t j = gw; j < (uint64_t)((jobs != nullptr) ? njobs : 1); j += nw) {
         const Job &jb = (jobs != nullptr) ? jobs[j] : s_single;
@@ -436,10 +436,9 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
     cp_async_wait_none();
 }
 
-constexpr int kDecompressCtaSmem = kWarpsPerCta * kWarpBytes;
-
 int decompress_grid(uint64_t total_chunks) {
-    return persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDtMixed>), kDecompressCtaSmem,
+    const int w = g_cta_warps[1];
+    return persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDtMixed>), w, w * kWarpBytes,
                                 g_ctas_per_sm[1], total_chunks);
 }
 
@@ -447,9 +446,10 @@ namespace {
 template <int kDt>
 void launch_decode(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
                    cudaStream_t stream) {
-    const int grid = persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDt>), kDecompressCtaSmem,
+    const int w = g_cta_warps[1], smem = w * kWarpBytes;
+    const int grid = persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDt>), w, smem,
                                           g_ctas_per_sm[1], total_chunks);
-    decompress_kernel<kDt><<<grid, kThreads, kDecompressCtaSmem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+    decompress_kernel<kDt><<<grid, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
 }
 }  // namespace
 

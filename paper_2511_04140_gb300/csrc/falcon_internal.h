@@ -5,13 +5,15 @@
 
 namespace falcon {
 
-constexpr int kWarpsPerCta = 4;
+// Warps per CTA of the persistent kernels: a launch parameter (falcon_set_cta_warps) that
+// changes no output byte; every warp works on its own chunks.  The launch bounds keep the
+// register budget of the default shape (4 warps, 4 CTAs per SM for compression; 3 CTAs per SM
+// of 4 warps for decompression) at every allowed shape.
+constexpr int kWarpsPerCta = 4;                 // default
 constexpr int kThreads = 32 * kWarpsPerCta;
+constexpr int kMaxCompressWarps = 16;           // 512 threads: 128 registers per thread
+constexpr int kMaxDecompressWarps = 12;         // 384 threads: 170 registers per thread
 constexpr uint32_t kMaxBlock = 1025;
-// Shared memory per warp: the staged chunk (<= 1025 * 8 bytes + one extra 16-byte unit)
-// and, later, the compressed record (<= 8211 bytes) at a 0..15 byte shift, + 4 spare.
-constexpr int kWarpSmem = 8256;
-constexpr int kCtaSmem = kWarpSmem * kWarpsPerCta;
 
 // Status codes (identical numbering to falcon_status in include/falcon.h).
 enum : uint32_t { kOk = 0, kErrInvalid = 1, kErrCapacity = 2, kErrCorrupt = 3, kErrCuda = 4,
@@ -70,9 +72,12 @@ int compress_args(const void *d_in, uint64_t n, int dtype, uint32_t block, void 
 // [1] decompress.  Set through falcon_set_launch_config.
 extern int g_ctas_per_sm[2];
 
-// Persistent grid of a kernel of kThreads threads and smem_bytes dynamic shared memory: as
-// many CTAs as fit (at most lim per SM when lim > 0), fewer when there is less work.
-int persistent_grid_size(const void *kernel, int smem_bytes, int lim, uint64_t total_chunks);
+// Warps per CTA used by the persistent grids; [0] compress, [1] decompress.
+extern int g_cta_warps[2];
+
+// Persistent grid of a kernel with `warps` warps per CTA and smem_bytes dynamic shared memory:
+// as many CTAs as fit (at most lim per SM when lim > 0), fewer when there is less work.
+int persistent_grid_size(const void *kernel, int warps, int smem_bytes, int lim, uint64_t total_chunks);
 
 // Grid size used for a launch over total_chunks work items (persistent, occupancy-bound).
 int compress_grid(uint64_t total_chunks);

@@ -99,6 +99,8 @@ def _load():
             L.falcon_batch_forget.argtypes = [vp]
             L.falcon_set_launch_config.restype = ci
             L.falcon_set_launch_config.argtypes = [ci, ci]
+            L.falcon_set_cta_warps.restype = ci
+            L.falcon_set_cta_warps.argtypes = [ci, ci]
             L.falcon_pipeline_compress.restype = ci
             L.falcon_pipeline_compress.argtypes = [vp, u64, ci, u32, u64, ci, vp, sz, vp, c.POINTER(sz)]
             L.falcon_pipeline_compress_with.restype = ci
@@ -256,6 +258,11 @@ def release() -> None:
 def set_launch_config(compress_ctas_per_sm: int = 0, decompress_ctas_per_sm: int = 0) -> None:
     """Caps the persistent grids at the given CTAs per SM (0 = occupancy limit)."""
     _check(_load().falcon_set_launch_config(compress_ctas_per_sm, decompress_ctas_per_sm), "set_launch_config")
+
+
+def set_cta_warps(compress_warps: int = 4, decompress_warps: int = 4) -> None:
+    """Warps per CTA of the persistent kernels (launch shape only, no output byte changes)."""
+    _check(_load().falcon_set_cta_warps(compress_warps, decompress_warps), "set_cta_warps")
 
 
 class Batch:

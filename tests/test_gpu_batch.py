@@ -112,3 +112,25 @@ def test_autotune_keeps_bytes(F, oracle):
             assert st.cpu().numpy().tobytes() == oracle.compress(s, blk)
     finally:
         F.set_launch_config(0, 0)
+
+
+def test_cta_shape_changes_no_byte(F, oracle):
+    """Warps per CTA and resident CTAs per SM are launch shape only: every shape the autotuner
+    may pick gives the oracle's bytes, in both directions."""
+    vals = synth.segments(300_001, seed=51)
+    x = torch.from_numpy(vals).cuda()
+    ref = oracle.compress(vals, 1024)
+    try:
+        for cw, dw, cc, dc in ((1, 1, 0, 0), (2, 12, 0, 0), (8, 3, 2, 1), (16, 8, 0, 2)):
+            F.set_cta_warps(cw, dw)
+            F.set_launch_config(cc, dc)
+            s = F.compress(x, 1024)
+            assert s.cpu().numpy().tobytes() == ref, (cw, dw, cc, dc)
+            y = F.decompress(s)
+            assert torch.equal(y.view(torch.int64), x.view(torch.int64)), (cw, dw, cc, dc)
+        for bad in ((0, 4), (17, 4), (4, 13)):
+            with pytest.raises(F.FalconError):
+                F.set_cta_warps(*bad)
+    finally:
+        F.set_cta_warps(4, 4)
+        F.set_launch_config(0, 0)
