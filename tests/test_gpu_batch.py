@@ -102,7 +102,8 @@ def test_autotune_keeps_bytes(F, oracle):
     xs = [torch.from_numpy(s).cuda() for s in series]
     out = tune.autotune(xs, blocks=(512, 1024), compress_ctas=(0, 1), decompress_ctas=(0, 1), reps=1)
     choice = out["choice"]
-    assert choice["block"] in (512, 1024) and len(out["table"]) == 8
+    # 2 blocks x 3 x 3 CTA shapes at the occupancy limit, then 3 resident-CTA caps
+    assert choice["block"] in (512, 1024) and len(out["table"]) == 2 * 3 * 3 + 3
     blk = tune.apply(choice)
     try:
         b = F.Batch(F.COMPRESS, xs, block=blk)
@@ -112,6 +113,7 @@ def test_autotune_keeps_bytes(F, oracle):
             assert st.cpu().numpy().tobytes() == oracle.compress(s, blk)
     finally:
         F.set_launch_config(0, 0)
+        F.set_cta_warps(4, 4)
 
 
 def test_cta_shape_changes_no_byte(F, oracle):
