@@ -1,6 +1,6 @@
 // Falcon compression (Sec. 3 of the paper; the work of Alg. 3 CmpKernel) for sm_103a, as
 // three launches, none of which waits on another warp:
-//   1. analyse: each warp takes chunks in a fixed stride (its one shared-memory value buffer
+//   1. analyse: each warp takes its chunks by ticket (its one shared-memory value buffer
 //      receives the next chunk by cp.async, swizzled, as soon as the Case decision is done)
 //      and computes
 //      - the lane's 32 values, specials (R1) and the chunk maximum,
@@ -663,11 +663,11 @@ __device__ __forceinline__ const Job &job_of(const Job *jobs, int njobs, const J
 // which the instruction caches notice.
 constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2;
 
-// Launch 1: analysis of every chunk (fixed stride per warp; the next chunk is copied into
+// Launch 1: analysis of every chunk (chunks by ticket; the next chunk is copied into
 // the warp's one value buffer while the current one is finished).
 template <int kDt>
 __global__ void __launch_bounds__(32 * kMaxCompressWarps, 1)
-analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
+analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -676,16 +676,17 @@ analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t tot
     __shared__ Job s_single;                      // the single job, read from shared memory
     if (threadIdx.x == 0) s_single = single;
     __syncthreads();
-    const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    if (gw >= total_chunks) return;
-    issue_chunk(jobs, njobs, s_single, gw, wbase, lane);
+    uint64_t t = ticket_of(take_ticket(ctl, kTicketAnalyse, lane));
+    if (t >= total_chunks) return;
+    issue_chunk(jobs, njobs, s_single, t, wbase, lane);
     cp_async_commit();
-    for (uint64_t t = gw; t < total_chunks; t += nw) {
-        const uint64_t tn = t + nw;
+    for (;;) {
+        const unsigned long long raw = take_ticket(ctl, kTicketAnalyse, lane);   // the chunk after t
+        uint64_t tn = total_chunks;
         cp_async_wait_none();                    // the current chunk has landed
         __syncwarp();
         auto next = [&]() {
+            tn = ticket_of(raw);
             if (tn < total_chunks) issue_chunk(jobs, njobs, s_single, tn, wbase, lane);
             cp_async_commit();
         };
@@ -696,6 +697,8 @@ analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t tot
         else if (job.dtype == 0) analyse_chunk<true>(job, c, wbase, scratch, lane, next);
         else analyse_chunk<false>(job, c, wbase, scratch, lane, next);
         __syncwarp();
+        if (tn >= total_chunks) break;
+        t = tn;
     }
     cp_async_wait_none();
 }
@@ -733,10 +736,10 @@ __device__ __forceinline__ EmitInfo load_info(const Job &job, uint64_t c, int la
     return e;
 }
 
-// Launch 3: the records (fixed stride per warp; the next chunk's values are prefetched into L2).
+// Launch 3: the records (chunks by ticket; the next chunk's values are prefetched into L2).
 template <bool kWide, int kDt>
 __global__ void __launch_bounds__(32 * kMaxCompressWarps, 1)
-emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks) {
+emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -744,16 +747,17 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
     __shared__ Job s_single;
     if (threadIdx.x == 0) s_single = single;
     __syncthreads();
-    const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    if (gw >= total_chunks) return;
+    uint64_t t = ticket_of(take_ticket(ctl, kTicketEmit, lane));
+    if (t >= total_chunks) return;
+    uint64_t tn = ticket_of(take_ticket(ctl, kTicketEmit, lane));
     EmitInfo info;
     {
-        const Job &j0 = job_of(jobs, njobs, s_single, gw);
-        info = load_info(j0, gw - j0.chunk_begin, lane);
+        const Job &j0 = job_of(jobs, njobs, s_single, t);
+        info = load_info(j0, t - j0.chunk_begin, lane);
     }
-    for (uint64_t t = gw; t < total_chunks; t += nw) {
-        const uint64_t tn = t + nw;
+    for (;;) {
+        // the ticket after tn, read at the next iteration; tn's values and words are fetched now
+        const unsigned long long raw = tn < total_chunks ? take_ticket(ctl, kTicketEmit, lane) : 0ull;
         EmitInfo next{};
         if (tn < total_chunks) {
             prefetch_chunk(jobs, njobs, s_single, tn, lane);
@@ -768,6 +772,9 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
         else if (job.dtype == 0) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
         else emit_chunk<false, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
         __syncwarp();
+        if (tn >= total_chunks) break;
+        t = tn;
+        tn = ticket_of(raw);
         info = next;
     }
     if (lane == 0) bulk_wait();
@@ -777,18 +784,20 @@ namespace {
 int persistent_grid_of(const void *kernel, int warps, int smem_bytes, int lim, uint64_t total_chunks);
 
 template <int kDt>
-void launch_analyse(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, cudaStream_t stream) {
+void launch_analyse(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
+                    cudaStream_t stream) {
     const int w = g_cta_warps[0], smem = w * kAnalyseWarpBytes;
     const int g = persistent_grid_of(reinterpret_cast<const void *>(analyse_kernel<kDt>), w, smem, g_ctas_per_sm[0],
                                      total_chunks);
-    analyse_kernel<kDt><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks);
+    analyse_kernel<kDt><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
 }
 template <bool kWide, int kDt>
-void launch_emit(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, cudaStream_t stream) {
+void launch_emit(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
+                 cudaStream_t stream) {
     const int w = g_cta_warps[0], smem = w * EmitLayout<kWide>::kBytes;
     const int g = persistent_grid_of(reinterpret_cast<const void *>(emit_kernel<kWide, kDt>), w, smem,
                                      g_ctas_per_sm[0], total_chunks);
-    emit_kernel<kWide, kDt><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks);
+    emit_kernel<kWide, kDt><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
 }
 
 // Resident CTAs per SM of a persistent kernel at one CTA shape, looked up once per (kernel,
@@ -833,22 +842,21 @@ int compress_grid(uint64_t total_chunks) {
 
 cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,
                             Control *ctl, cudaStream_t stream) {
-    (void)ctl;
     // the every-row-sparse ablation writes records larger than the plane slots hold
     const bool wide = d_jobs == nullptr && single.variant == kVariantSparse;
     const int kind = d_jobs != nullptr ? kDtMixed : (single.dtype == 0 ? kDtF64 : kDtF32);
     if (total_chunks > 0) {
-        if (kind == kDtF64) launch_analyse<kDtF64>(d_jobs, njobs, single, total_chunks, stream);
-        else if (kind == kDtF32) launch_analyse<kDtF32>(d_jobs, njobs, single, total_chunks, stream);
-        else launch_analyse<kDtMixed>(d_jobs, njobs, single, total_chunks, stream);
+        if (kind == kDtF64) launch_analyse<kDtF64>(d_jobs, njobs, single, total_chunks, ctl, stream);
+        else if (kind == kDtF32) launch_analyse<kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
+        else launch_analyse<kDtMixed>(d_jobs, njobs, single, total_chunks, ctl, stream);
     }
     compress_offsets_kernel<<<(d_jobs != nullptr) ? njobs : 1, 1024, 0, stream>>>(d_jobs, single);
     if (total_chunks > 0) {
-        if (wide && kind == kDtF64) launch_emit<true, kDtF64>(d_jobs, njobs, single, total_chunks, stream);
-        else if (wide) launch_emit<true, kDtF32>(d_jobs, njobs, single, total_chunks, stream);
-        else if (kind == kDtF64) launch_emit<false, kDtF64>(d_jobs, njobs, single, total_chunks, stream);
-        else if (kind == kDtF32) launch_emit<false, kDtF32>(d_jobs, njobs, single, total_chunks, stream);
-        else launch_emit<false, kDtMixed>(d_jobs, njobs, single, total_chunks, stream);
+        if (wide && kind == kDtF64) launch_emit<true, kDtF64>(d_jobs, njobs, single, total_chunks, ctl, stream);
+        else if (wide) launch_emit<true, kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
+        else if (kind == kDtF64) launch_emit<false, kDtF64>(d_jobs, njobs, single, total_chunks, ctl, stream);
+        else if (kind == kDtF32) launch_emit<false, kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
+        else launch_emit<false, kDtMixed>(d_jobs, njobs, single, total_chunks, ctl, stream);
     }
     return cudaGetLastError();
 }

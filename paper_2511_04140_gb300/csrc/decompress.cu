@@ -2,7 +2,7 @@
 //
 // 1. offsets_kernel: the chunk-size array is read and its exclusive prefix (the chunk
 //    offset array) is written to the workspace - the step Sec. 4 performs first.
-// 2. decompress_kernel: persistent; warp w decodes chunks w, w + W, w + 2W, ... (no
+// 2. decompress_kernel: persistent; each warp takes its chunks by ticket (one atomic add each; no
 //    ordering constraint remains).  Each warp has one record buffer: the cp.async of its
 //    next record starts as soon as the current one has been expanded into the plane buffer;
 //    offsets are loaded one step earlier still.  Decoding a record:
@@ -397,20 +397,23 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
     __syncthreads();
     const uint64_t gw = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
-    (void)ctl;
     for (uint64_t j = gw; j < (uint64_t)((jobs != nullptr) ? njobs : 1); j += nw) {
         const Job &jb = (jobs != nullptr) ? jobs[j] : s_single;
         if (lane == 0) jb.result[0] = jb.n;
     }
-    if (gw >= total_chunks) return;
-    Loc lc = locate(jobs, njobs, s_single, gw, lane);
+    // chunk tickets two deep: t is decoded, tn's record is fetched during t, tnn is located
+    uint64_t t = ticket_of(take_ticket(ctl, kTicketDecode, lane));
+    if (t >= total_chunks) return;
+    uint64_t tn = ticket_of(take_ticket(ctl, kTicketDecode, lane));
+    Loc lc = locate(jobs, njobs, s_single, t, lane);
     resolve(jobs, njobs, s_single, lc);
-    bool okc = issue_record(job_of(jobs, njobs, s_single, gw), lc, wbase, lane);
+    bool okc = issue_record(job_of(jobs, njobs, s_single, t), lc, wbase, lane);
     cp_async_commit();
     Loc ln{};
-    if (gw + nw < total_chunks) ln = locate(jobs, njobs, s_single, gw + nw, lane);
-    for (uint64_t t = gw; t < total_chunks; t += nw) {
-        const uint64_t tn = t + nw;
+    if (tn < total_chunks) ln = locate(jobs, njobs, s_single, tn, lane);
+    for (;;) {
+        const unsigned long long raw = tn < total_chunks ? take_ticket(ctl, kTicketDecode, lane) : 0ull;
+        uint64_t tnn = total_chunks;
         bool okn = false;
         Loc lnn{};
         cp_async_wait_none();                    // the current record has landed
@@ -418,9 +421,10 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
         // the next record goes into the same buffer once this one has been read
         auto next = [&]() {
             if (tn < total_chunks) {
+                tnn = ticket_of(raw);
                 resolve(jobs, njobs, s_single, ln);
                 okn = issue_record(job_of(jobs, njobs, s_single, tn), ln, wbase, lane);
-                if (tn + nw < total_chunks) lnn = locate(jobs, njobs, s_single, tn + nw, lane);
+                if (tnn < total_chunks) lnn = locate(jobs, njobs, s_single, tnn, lane);
             }
             cp_async_commit();
         };
@@ -429,6 +433,9 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
         else if constexpr (kDt == kDtF32) decode_chunk<false>(job, lc, okc, wbase, pbuf, lane, next);
         else if (job.dtype == 0) decode_chunk<true>(job, lc, okc, wbase, pbuf, lane, next);
         else decode_chunk<false>(job, lc, okc, wbase, pbuf, lane, next);
+        if (tn >= total_chunks) break;
+        t = tn;
+        tn = tnn;
         lc = ln;
         okc = okn;
         ln = lnn;

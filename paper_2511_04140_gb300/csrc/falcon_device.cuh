@@ -561,6 +561,14 @@ __device__ __forceinline__ int find_job(const Job *jobs, int njobs, uint64_t t) 
     return lo;
 }
 
+// Chunk tickets (Control): take_ticket issues lane 0's atomic add and returns its raw result
+// (valid in lane 0 only); ticket_of broadcasts it.  Issuing the atomic a chunk before its result
+// is read hides the atomic's latency behind the current chunk.
+__device__ __forceinline__ unsigned long long take_ticket(Control *ctl, int which, int lane) {
+    return lane == 0 ? atomicAdd(&ctl->ticket[which], 1ull) : 0ull;
+}
+__device__ __forceinline__ uint64_t ticket_of(unsigned long long raw) { return shfl_u64(raw, 0); }
+
 __device__ __forceinline__ uint32_t chunk_cols(uint32_t m) { return m <= 1 ? 0u : ((m - 1u + 63u) & ~63u); }
 
 }  // namespace falcon

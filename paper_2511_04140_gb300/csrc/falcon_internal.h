@@ -41,12 +41,14 @@ struct Job {
 // row dense, Elf's trial-and-error decimal place).  All write the same record layout.
 enum : uint32_t { kVariantFalcon = 0, kVariantSparse = 1, kVariantDense = 2, kVariantElf = 3 };
 
-// Per-launch control block at the start of the workspace (zeroed before each launch); the
-// kernels of this version take their chunks in a fixed stride and do not use its fields.
+// Per-launch control block at the start of the workspace (zeroed before each set of launches):
+// the chunk tickets of the persistent kernels.  A warp takes its next chunk with one atomic
+// add on its kernel's counter (analysis, emit, decode), so warps that met cheaper chunks take
+// more of them and a launch ends with its average warp, not its unluckiest one.
+enum { kTicketAnalyse = 0, kTicketEmit = 1, kTicketDecode = 2 };
 struct Control {
-    unsigned long long ticket;     // reserved
-    unsigned int abort;            // reserved
-    unsigned int pad[13];
+    unsigned long long ticket[4];
+    unsigned int pad[8];
 };
 static_assert(sizeof(Control) == 64, "control block is 64 bytes");
 
