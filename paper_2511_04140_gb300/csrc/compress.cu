@@ -189,8 +189,9 @@ __device__ __noinline__ int search_alpha(const uint8_t *buf, int lane, uint32_t 
 // FP32: alpha_max = max over values of Alg. 2's decimal place (the first a with eps <= mu,
 // accepted only if the round trip holds there), restricted to [0, atop], then the R6 check
 // that every value round-trips at alpha_max; -1 means Case 2.  The values are tested a
-// decimal place at a time, all of a lane's together (no divergent per-value loops).
-__device__ __noinline__ int alpha32(const uint8_t *buf, int lane, uint32_t m, uint32_t vx, bool has_vx, int atop) {
+// decimal place at a time, all of a lane's together (no divergent per-value loops).  Inlined:
+// as a call it made the caller save its live registers to the stack around it.
+__device__ __forceinline__ int alpha32(const uint8_t *buf, int lane, uint32_t m, uint32_t vx, bool has_vx, int atop) {
     uint32_t v[32];
 #pragma unroll
     for (int k = 0; k < 32; ++k) v[k] = 32u * lane + k < m ? lane_value<false>(buf, lane, k) : 0u;

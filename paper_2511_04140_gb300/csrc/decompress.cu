@@ -421,9 +421,9 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
         // the next record goes into the same buffer once this one has been read
         auto next = [&]() {
             if (tn < total_chunks) {
-                tnn = ticket_of(raw);
                 resolve(jobs, njobs, s_single, ln);
                 okn = issue_record(job_of(jobs, njobs, s_single, tn), ln, wbase, lane);
+                tnn = ticket_of(raw);
                 if (tnn < total_chunks) lnn = locate(jobs, njobs, s_single, tnn, lane);
             }
             cp_async_commit();
