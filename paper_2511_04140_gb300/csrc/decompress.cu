@@ -22,11 +22,15 @@ namespace falcon {
 
 namespace {
 
-// one record at a 0..15 byte phase, + 16 readable bytes: an FP64 record is at most
-// 19 + 64 * 144 = 9235 bytes (every row sparse without a zero byte: bitmap + 128 bytes)
-constexpr int kBuf = 9280;
-constexpr int kPlane = 8192 + 128;          // 64 plane slots of 128 bytes + 64 u16 sparse-byte totals
-constexpr int kWarpBytes = kBuf + kPlane;
+// Per-warp buffers of a kernel form: one record at a 0..15 byte phase + 16 readable bytes (an
+// FP64 record is at most 19 + 64 * 144 = 9235 bytes, an FP32 one 11 + 32 * 144 = 4619: every
+// row sparse without a zero byte, bitmap + 128 bytes), then W plane slots of 128 bytes and 64
+// u16 sparse-byte totals.  The FP32 form's smaller buffers let more warps stay resident.
+template <bool F64> struct DecLayout {
+    static constexpr int kBuf = F64 ? 9280 : 4672;
+    static constexpr int kPlane = (F64 ? 64 : 32) * 128 + 128;
+    static constexpr int kWarpBytes = kBuf + kPlane;
+};
 
 // Byte-permute selector that spreads a lane's compacted non-zero bytes over its four row
 // bytes, by bitmap nibble n: row byte i (nibble bit 3 - i) takes the next compacted byte if
@@ -160,7 +164,9 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     const uint32_t size = l.size;
     const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(job.in + l.rec_off) & 15u);
     const uint8_t *rec = rbuf + sh;
-    uint16_t *rowpos = reinterpret_cast<uint16_t *>(pbuf + 8192);
+    // plane p lives in slot W - 1 - p of pbuf: slot addresses are written planes + (63 - p) * 128
+    uint8_t *planes = pbuf - (64 - T::W) * 128;
+    uint16_t *rowpos = reinterpret_cast<uint16_t *>(pbuf + T::W * 128);
 
     // ---- a. header, flags, row positions; sparse rows expanded ---------------------------
     bool bad = !loc_ok;
@@ -216,7 +222,7 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
         const uint32_t *wq = reinterpret_cast<const uint32_t *>(rbuf + (qa & ~3u));
         const uint32_t word = __funnelshift_r(wq[0], wq[1], (qa & 3u) * 8u);
         const uint32_t x = __byte_perm(word, 0u, s_expand_sel[nib]);
-        *reinterpret_cast<uint32_t *>(pbuf + (63 - p) * 128 + 4 * lane) = x;
+        *reinterpret_cast<uint32_t *>(planes + (63 - p) * 128 + 4 * lane) = x;
         sparse_sum += bm_bytes + nnz;
         if (lane == 0) rowpos[p] = (uint16_t)sparse_sum;   // sparse bytes through row p
     }
@@ -244,7 +250,7 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
             // sparse bytes above p: the running total at the lowest sparse row above p
             const uint32_t sbytes = sp_above ? (uint32_t)rowpos[__ffsll((long long)sp_above) - 1] : 0u;
             const uint32_t rp = hdr + row_bytes * (uint32_t)__popcll(dense_mask & above) + sbytes;
-            copy_to_planes(pbuf + (63 - p) * 128, rec + rp, (uint32_t)(p - q + 1) * row_bytes, lane);
+            copy_to_planes(planes + (63 - p) * 128, rec + rp, (uint32_t)(p - q + 1) * row_bytes, lane);
             dm &= (q > 0) ? ((1ull << q) - 1ull) : 0ull;
         }
     }
@@ -255,7 +261,7 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     // chunks) gather stale words too; their columns lie past the chunk's values and are never
     // stored, and they only feed the scan of later lanes.
     auto plane_word = [&](int p) -> uint32_t {
-        return *reinterpret_cast<const uint32_t *>(pbuf + (63 - p) * 128 + 4 * lane);
+        return *reinterpret_cast<const uint32_t *>(planes + (63 - p) * 128 + 4 * lane);
     };
     U d[32];
     if constexpr (F64) {
@@ -389,8 +395,9 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    uint8_t *wbase = smem + warp * kWarpBytes;
-    uint8_t *pbuf = wbase + kBuf;
+    using L = DecLayout<kDt != kDtF32>;
+    uint8_t *wbase = smem + warp * L::kWarpBytes;
+    uint8_t *pbuf = wbase + L::kBuf;
     __shared__ Job s_single;                      // the single job, read from shared memory
     if (threadIdx.x == 0) s_single = single;
     init_expand_sel();
@@ -445,7 +452,8 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
 
 int decompress_grid(uint64_t total_chunks) {
     const int w = g_cta_warps[1];
-    return persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDtMixed>), w, w * kWarpBytes,
+    return persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDtMixed>), w,
+                                w * DecLayout<true>::kWarpBytes,
                                 g_ctas_per_sm[1], total_chunks);
 }
 
@@ -453,7 +461,7 @@ namespace {
 template <int kDt>
 void launch_decode(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
                    cudaStream_t stream) {
-    const int w = g_cta_warps[1], smem = w * kWarpBytes;
+    const int w = g_cta_warps[1], smem = w * DecLayout<kDt != kDtF32>::kWarpBytes;
     const int grid = persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDt>), w, smem,
                                           g_ctas_per_sm[1], total_chunks);
     decompress_kernel<kDt><<<grid, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
