@@ -739,15 +739,11 @@ __device__ __forceinline__ EmitInfo load_info(const Job &job, uint64_t c, int la
 
 // Launch 3: the records (chunks by ticket; the next chunk's values are prefetched into L2).
 template <bool kWide, int kDt>
-__global__ void __launch_bounds__(32 * kMaxCompressWarps, 1)
-emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
-    extern __shared__ __align__(16) uint8_t smem[];
+__device__ __forceinline__ void emit_loop(const Job *__restrict__ jobs, int njobs, const Job &s_single,
+                                          uint64_t total_chunks, Control *ctl, uint8_t *smem) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     uint8_t *wbase = smem + warp * EmitLayout<kWide>::kBytes;
-    __shared__ Job s_single;
-    if (threadIdx.x == 0) s_single = single;
-    __syncthreads();
     uint64_t t = ticket_of(take_ticket(ctl, kTicketEmit, lane));
     if (t >= total_chunks) return;
     uint64_t tn = ticket_of(take_ticket(ctl, kTicketEmit, lane));
@@ -781,6 +777,28 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
     if (lane == 0) bulk_wait();
 }
 
+// FP64 and either-dtype forms (up to 128 registers, 16 warps per SM)
+template <bool kWide, int kDt>
+__global__ void __launch_bounds__(32 * kMaxCompressWarps, 1)
+emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ Job s_single;
+    if (threadIdx.x == 0) s_single = single;
+    __syncthreads();
+    emit_loop<kWide, kDt>(jobs, njobs, s_single, total_chunks, ctl, smem);
+}
+
+// FP32 form: held to 96 registers (it needs 93 without spilling), so that 20 warps fit an SM
+template <bool kWide>
+__global__ void __maxnreg__(96)
+emit_kernel_f32(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ Job s_single;
+    if (threadIdx.x == 0) s_single = single;
+    __syncthreads();
+    emit_loop<kWide, kDtF32>(jobs, njobs, s_single, total_chunks, ctl, smem);
+}
+
 namespace {
 int persistent_grid_of(const void *kernel, int warps, int smem_bytes, int lim, uint64_t total_chunks);
 
@@ -796,9 +814,15 @@ template <bool kWide, int kDt>
 void launch_emit(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
                  cudaStream_t stream) {
     const int w = g_cta_warps[0], smem = w * EmitLayout<kWide>::kBytes;
-    const int g = persistent_grid_of(reinterpret_cast<const void *>(emit_kernel<kWide, kDt>), w, smem,
-                                     g_ctas_per_sm[0], total_chunks);
-    emit_kernel<kWide, kDt><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+    if constexpr (kDt == kDtF32) {
+        const int g = persistent_grid_of(reinterpret_cast<const void *>(emit_kernel_f32<kWide>), w, smem,
+                                         g_ctas_per_sm[0], total_chunks);
+        emit_kernel_f32<kWide><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+    } else {
+        const int g = persistent_grid_of(reinterpret_cast<const void *>(emit_kernel<kWide, kDt>), w, smem,
+                                         g_ctas_per_sm[0], total_chunks);
+        emit_kernel<kWide, kDt><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+    }
 }
 
 // Resident CTAs per SM of a persistent kernel at one CTA shape, looked up once per (kernel,
