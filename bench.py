@@ -332,7 +332,7 @@ def profiled_traffic(kernel: str):
     import re
     here = os.path.dirname(os.path.abspath(__file__))
     try:
-        text = open(os.path.join(here, "profiles", "dram_traffic_segments_2e25.md")).read()
+        text = open(os.path.join(here, "profiles", "dram_traffic_segments_2e26.md")).read()
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_call " + re.escape(kernel) + r" (\d+) sources ([0-9a-f]+)", text)
