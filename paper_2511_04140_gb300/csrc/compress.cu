@@ -186,41 +186,39 @@ __device__ __noinline__ int search_alpha(const uint8_t *buf, int lane, uint32_t 
     }
 }
 
-// FP32: alpha_max = max over values of Alg. 2's decimal place (the first a with eps <= mu,
-// accepted only if the round trip holds there), restricted to [0, atop], then the R6 check
-// that every value round-trips at alpha_max; -1 means Case 2.  The values are tested a
-// decimal place at a time, all of a lane's together (no divergent per-value loops).  Inlined:
-// as a call it made the caller save its live registers to the stack around it.
-__device__ __forceinline__ int alpha32(const uint8_t *buf, int lane, uint32_t m, uint32_t vx, bool has_vx, int atop) {
-    uint32_t v[32];
+// FP32 chunks at beta_hat = 7 (R14): Alg. 2, value by value, stops at the first decimal place
+// where eps <= mu passes, and if the round trip fails there the value is an exception.  That
+// can happen below a value's own decimal place k only if |v| 10^k >= 2^23 / 1.5: with d / 10^k
+// its shortest decimal, v 10^a (a < k) lies at least 10^-(k-a) - |v| 10^a 2^-24 from every
+// integer, more than mu = |v 10^a| 2^-23 below that bound (checked exhaustively over every
+// decimal below it).  k <= alpha, so a value can stop early only if 3 |v| 10^alpha >= 2^23 (half
+// the bound, as a margin); only those values go through Alg. 2, and none when v_max is below.
+__device__ __forceinline__ bool may_stop_early(uint32_t u, int a) {
+    const uint32_t au = u & 0x7FFFFFFFu;
+    if (au == 0) return false;
+    if (au < 0x00800000u) return true;          // subnormal: take the full test
+    const int E = (int)(au >> 23) - 150;
+    const uint64_t p = 3ull * ((au & 0x007FFFFFu) | 0x00800000u) * FALCON_POW5[a];   // < 2^50
+    const int s = 23 - E - a;                    // 3 m 5^a 2^(E+a) >= 2^23  <=>  p >= 2^s
+    return s <= 0 || (s < 50 && p >= (1ull << s));
+}
+
+// True if some value of the chunk stops early (the chunk then takes Case 2); alpha is the
+// search's alpha_max, at which every value round-trips.
+__device__ __forceinline__ bool early_stop32(const uint8_t *buf, int lane, uint32_t m, const uint32_t (&v)[32],
+                                             uint32_t vx, bool has_vx, uint32_t vmax, int alpha) {
+    if (!may_stop_early(vmax, alpha)) return false;
+    uint32_t cand = 0;
 #pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = 32u * lane + k < m ? lane_value<false>(buf, lane, k) : 0u;
-    uint32_t open = 0xFFFFFFFFu;                // values of this lane still without a decimal place
-    bool open_x = has_vx;
-    bool bad = false;
-    int amax = 0;
+    for (int k = 0; k < 32; ++k) cand |= (uint32_t)(32u * lane + k < m && may_stop_early(v[k], alpha)) << k;
+    bool bad = has_vx && may_stop_early(vx, alpha) && first_pass_f32(vx, alpha) < 0;
 #pragma unroll 1
-    for (int a = 0; a <= atop; ++a) {
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            bool rt;
-            if (alg2_step_f32(v[k], a, rt) && ((open >> k) & 1u)) {
-                open &= ~(1u << k);
-                bad |= !rt;
-                amax = a;
-            }
-        }
-        bool rt;
-        if (alg2_step_f32(vx, a, rt) && open_x) {
-            open_x = false;
-            bad |= !rt;
-            amax = a;
-        }
-        if (!__any_sync(kFull, open != 0u || open_x)) break;
+    while (cand) {
+        const int k = __ffs(cand) - 1;
+        cand &= cand - 1;
+        bad |= first_pass_f32(lane_value<false>(buf, lane, k), alpha) < 0;
     }
-    if (__any_sync(kFull, bad || open != 0u || open_x)) return -1;
-    amax = (int)__reduce_max_sync(kFull, (uint32_t)amax);
-    return all_pass<false>(buf, lane, m, vx, amax) ? amax : -1;
+    return __any_sync(kFull, bad);
 }
 
 // Fal._Elf's decimal place of one value (Sec. 1's trial and error, ablation of Sec. 5.4.2):
@@ -410,13 +408,12 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
                 else fail = first_pass_f32(vmax, atop) < 0;
                 if (!fail) {
                     alpha = search_alpha<F64>(buf, lane, m, vx, atop);
-                    // FP32 (R14): with beta <= 6 no value can pass eps <= mu below its decimal
-                    // place (the distance to the nearest integer exceeds 1.5 * 2^-23 |x|), so
-                    // Alg. 2 value by value gives the same alpha_max; at beta_hat = 7 an early
-                    // pass is possible and the values go through Alg. 2 one by one.
+                    // FP32 (R14): below beta_hat = 7 no value can stop early (see
+                    // early_stop32), so Alg. 2 value by value gives the same alpha_max
                     if constexpr (!F64) {
-                        if (alpha >= 0 && alpha + e_max + 1 == T::B_MAX)
-                            alpha = alpha32(buf, lane, m, vx, m > 1024u && lane == 31, atop);
+                        if (alpha >= 0 && alpha + e_max + 1 == T::B_MAX &&
+                            early_stop32(buf, lane, m, v, vx, m > 1024u && lane == 31, vmax, alpha))
+                            alpha = -1;
                     }
                 }
             }
