@@ -160,7 +160,7 @@ int falcon_compress_variant_async(const void *d_in, uint64_t n, int dtype, uint3
 /* Allocation-free compression.  The paper has no counterpart: it is a deployment variant of
  * falcon_compress_async whose scratch (control block and per-chunk words) is a file-scope
  * static device array of the library, sized for FALCON_NOALLOC_MAX_CHUNKS chunks
- * (1,057,024 bytes per device; 67,108,864 values at block_size 1024), instead of a workspace.
+ * (1,057,280 bytes per device; 67,108,864 values at block_size 1024), instead of a workspace.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
  *   - The first call on a device looks the array's address up (cudaGetSymbolAddress, with
  *     that device current) and keeps it; make that first call before any stream capture.

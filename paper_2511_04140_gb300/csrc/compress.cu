@@ -1,24 +1,25 @@
 // Falcon compression (Sec. 3 of the paper; the work of Alg. 3 CmpKernel) for sm_103a, as
-// three launches, none of which waits on another warp:
+// two launches, neither of which waits on another warp:
 //   1. analyse: each warp takes its chunks by ticket (its one shared-memory value buffer
 //      receives the next chunk by cp.async, swizzled, as soon as the Case decision is done)
 //      and computes
 //      - the lane's 32 values, specials (R1) and the chunk maximum,
 //      - Case 1 / Case 2 of Eq. 4: the smallest decimal place alpha_max at which every value
-//        passes Alg. 2's test, in exact integer arithmetic (q_test); FP32 follows Alg. 2
-//        value by value,
+//        passes Alg. 2's test, in exact integer arithmetic (q_test); FP32 checks Alg. 2's
+//        early stops where they are possible,
 //      - G (Eq. 4), Z (Eq. 5) and the bit width w in registers,
 //      - the non-zero bytes of every row (Sec. 3.3 lambda) from ORs of 8-column groups,
 //        without forming the bit planes, sparse/dense per row, the record size, which goes
-//        into the stream's size array, and alpha, beta_hat, w and the dense-row mask, which
-//        go into the workspace;
-//   2. offsets: the exclusive prefix of each job's size array (the size synchronisation of
-//      Sec. 3.4), the stream header and length and the capacity check;
-//   3. emit: the values again (straight from global memory, the next chunk prefetched into
-//      L2), G, Z and the bit planes (32x32 register transposes, one 32-bit word per plane: 4
-//      row bytes per lane) from the kept alpha and w, the record assembled in shared memory at
-//      the output's 16-byte phase, in place of the plane words it consumes, and sent to its
-//      offset with one TMA bulk copy.
+//        into the stream's size array and is added to its 64-chunk tile's and 4096-chunk
+//        group's sums (the size synchronisation of Sec. 3.4), and alpha, beta_hat, w and the
+//        dense-row mask, which go into the workspace;
+//   2. emit: each chunk's record offset from those sums, the values again (straight from
+//      global memory, the next chunk prefetched into L2), G, Z and the bit planes (32x32
+//      register transposes, one 32-bit word per plane: 4 row bytes per lane) from the kept
+//      alpha and w, the record assembled in shared memory at the output's 16-byte phase, in
+//      place of the plane words it consumes, and sent to its offset with one TMA bulk copy;
+//      the warp of each job's first chunk writes the header and the stream length and checks
+//      the capacity.
 // The paper resolves offsets inside one launch with a decoupled look-back; with about 1800
 // resident warps on a GB300 the waits of that look-back took half of every warp's time, while
 // the analysis recomputed by the emit launch costs less.
@@ -284,7 +285,8 @@ __device__ __forceinline__ void issue_chunk(const Job *jobs, int njobs, const Jo
 // Workspace words of a job (job.flags), written by the analysis launch:
 //   flags[c]            alpha byte (5 bits) | beta_hat (5) | w (7), in bits 47..63;
 //   flags[nchunks + c]  the dense-row mask (bit p: plane p is stored dense);
-// then, from the offsets launch, flags[2 nchunks + j] = the record offset of 64-chunk tile j.
+//   flags[2 nchunks + j]                       the sum of the record sizes of 64-chunk tile j,
+//   flags[2 nchunks + tile_count(nchunks) + g]  and of 4096-chunk group g (atomic adds).
 constexpr int kMetaShift = 47;
 
 __device__ __forceinline__ unsigned long long pack_meta(int alpha_byte, int beta_hat, int w) {
@@ -490,6 +492,9 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
         reinterpret_cast<uint32_t *>(job.out + 32)[c] = size;
         job.flags[c] = pack_meta(alpha >= 0 ? alpha : T::A_SENT, beta_hat, w);
         job.flags[job.nchunks + c] = dense_mask;
+        unsigned long long *tsum = job.flags + 2 * job.nchunks;
+        atomicAdd(tsum + c / kTile, (unsigned long long)size);
+        atomicAdd(tsum + tile_count(job.nchunks) + c / kGroup, (unsigned long long)size);
     }
 }
 
@@ -554,7 +559,7 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     const int alpha_byte = (int)(mb >> 12), beta_hat = (int)((mb >> 7) & 31u), w = (int)(mb & 127u);
     const int alpha = alpha_byte == T::A_SENT ? -1 : alpha_byte;
     const uint64_t rec_off = data_start + rel;
-    if (rec_off + size > job.out_cap) return;    // the offsets launch reported the capacity error
+    if (rec_off + size > job.out_cap) return;    // the job's first chunk reports the capacity error
 
     // ---- G, Z and the plane words in shared memory --------------------------------------------
     const uint8_t *src = job.in + first * T::S;
@@ -701,16 +706,15 @@ analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t tot
     cp_async_wait_none();
 }
 
-// Launch 2: record offsets per 64-chunk tile (exclusive prefix of each job's size array),
-// the stream header, the stream length and the capacity check; one CTA per job.
-__global__ void __launch_bounds__(1024)
-compress_offsets_kernel(const Job *__restrict__ jobs, Job single) {
-    __shared__ uint64_t warp_sums[33];
-    const Job &job = (jobs == nullptr) ? single : jobs[blockIdx.x];
+// Stream header, stream length and capacity check of one job (one warp): the length is the
+// header, the size array and the records, whose sizes the analysis added up per group.
+__device__ void finish_job(const Job &job, int lane) {
     const uint64_t nc = job.nchunks;
-    const uint64_t total = tile_prefix(reinterpret_cast<const uint32_t *>(job.out + 32), nc, job.flags + 2 * nc,
-                                       warp_sums);
-    if (threadIdx.x == 0) {
+    const unsigned long long *gsum = job.flags + 2 * nc + tile_count(nc);
+    uint64_t part = 0;
+    for (uint64_t g = (uint64_t)lane; g < group_count(nc); g += 32) part += gsum[g];
+    const uint64_t total = warp_sum_u64(part);
+    if (lane == 0) {
         const uint64_t bytes = 32ull + 4ull * nc + total;
         job.result[0] = bytes;
         if (bytes > job.out_cap) set_status(job.result, kErrCapacity);
@@ -720,18 +724,41 @@ compress_offsets_kernel(const Job *__restrict__ jobs, Job single) {
     }
 }
 
-// Per-chunk words of the emit launch, loaded one chunk ahead.
+// Where chunk c's record starts, relative to the first record (Sec. 3.4's size synchronisation,
+// from the analysis' sums): the groups before c's group, the tiles of its group before its tile
+// and the chunks of its tile before it.  Loaded one chunk ahead (every lane), added up when
+// needed.  A group's records take < 2^26 bytes and two tiles and two records < 2^22, so a lane's
+// share stays below 2^32 up to 63 groups per lane (8 M chunks); the warp then adds its 16-bit
+// halves with two 32-bit reductions, and larger shares in 64 bits.
 struct EmitInfo {
     unsigned long long meta, dense;
-    ChunkPos pos;
+    uint64_t part;                    // this lane's share of the earlier records' bytes
+    uint32_t size;                    // c's record size
 };
 
 __device__ __forceinline__ EmitInfo load_info(const Job &job, uint64_t c, int lane) {
+    const uint64_t nc = job.nchunks;
+    const uint32_t *sizes = reinterpret_cast<const uint32_t *>(job.out + 32);
+    const unsigned long long *tsum = job.flags + 2 * nc, *gsum = tsum + tile_count(nc);
     EmitInfo e;
     e.meta = job.flags[c];
-    e.dense = job.flags[job.nchunks + c];
-    e.pos = load_pos(reinterpret_cast<const uint32_t *>(job.out + 32), job.flags + 2 * job.nchunks, c, lane);
+    e.dense = job.flags[nc + c];
+    e.size = sizes[c];
+    const uint64_t g = c / kGroup, t = c / kTile, tb = g * (kGroup / kTile), cb = t * kTile;
+    uint64_t part = 0;
+    for (uint64_t j = (uint64_t)lane; j < g; j += 32) part += gsum[j];
+    if (tb + (uint64_t)lane < t) part += tsum[tb + lane];
+    if (tb + 32u + (uint64_t)lane < t) part += tsum[tb + 32u + lane];
+    if (cb + (uint64_t)lane < c) part += sizes[cb + lane];
+    if (cb + 32u + (uint64_t)lane < c) part += sizes[cb + 32u + lane];
+    e.part = part;
     return e;
+}
+__device__ __forceinline__ uint64_t resolve_info(const EmitInfo &e) {
+    if (__any_sync(kFull, (e.part >> 32) != 0)) return warp_sum_u64(e.part);
+    const uint32_t p = (uint32_t)e.part;
+    const uint32_t lo = __reduce_add_sync(kFull, p & 0xFFFFu), hi = __reduce_add_sync(kFull, p >> 16);
+    return (uint64_t)lo + ((uint64_t)hi << 16);
 }
 
 // Launch 3: the records (chunks by ticket; the next chunk's values are prefetched into L2).
@@ -741,6 +768,20 @@ __device__ __forceinline__ void emit_loop(const Job *__restrict__ jobs, int njob
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     uint8_t *wbase = smem + warp * EmitLayout<kWide>::kBytes;
+    if (blockIdx.x == 0 && warp == 0) {          // jobs without chunks: header and length only
+        if (jobs == nullptr) {
+            if (s_single.nchunks == 0) finish_job(s_single, lane);
+        } else {
+            for (int j0 = 0; j0 < njobs; j0 += 32) {
+                unsigned empty = __ballot_sync(kFull, j0 + lane < njobs && jobs[j0 + lane].nchunks == 0);
+                while (empty) {
+                    const int j = j0 + __ffs(empty) - 1;
+                    empty &= empty - 1;
+                    finish_job(jobs[j], lane);
+                }
+            }
+        }
+    }
     uint64_t t = ticket_of(take_ticket(ctl, kTicketEmit, lane));
     if (t >= total_chunks) return;
     uint64_t tn = ticket_of(take_ticket(ctl, kTicketEmit, lane));
@@ -760,11 +801,12 @@ __device__ __forceinline__ void emit_loop(const Job *__restrict__ jobs, int njob
         }
         const Job &job = job_of(jobs, njobs, s_single, t);
         const uint64_t c = t - job.chunk_begin;
-        const uint64_t rel = resolve_pos(info.pos);
-        if constexpr (kDt == kDtF64) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
-        else if constexpr (kDt == kDtF32) emit_chunk<false, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
-        else if (job.dtype == 0) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
-        else emit_chunk<false, kWide>(job, c, wbase, lane, info.meta, info.dense, info.pos.size, rel);
+        const uint64_t rel = resolve_info(info);
+        if (c == 0) finish_job(job, lane);
+        if constexpr (kDt == kDtF64) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
+        else if constexpr (kDt == kDtF32) emit_chunk<false, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
+        else if (job.dtype == 0) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
+        else emit_chunk<false, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
         __syncwarp();
         if (tn >= total_chunks) break;
         t = tn;
@@ -872,8 +914,7 @@ cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single, uin
         else if (kind == kDtF32) launch_analyse<kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
         else launch_analyse<kDtMixed>(d_jobs, njobs, single, total_chunks, ctl, stream);
     }
-    compress_offsets_kernel<<<(d_jobs != nullptr) ? njobs : 1, 1024, 0, stream>>>(d_jobs, single);
-    if (total_chunks > 0) {
+    {   // the emit launch also writes the header and length of every job, chunks or none
         if (wide && kind == kDtF64) launch_emit<true, kDtF64>(d_jobs, njobs, single, total_chunks, ctl, stream);
         else if (wide) launch_emit<true, kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
         else if (kind == kDtF64) launch_emit<false, kDtF64>(d_jobs, njobs, single, total_chunks, ctl, stream);

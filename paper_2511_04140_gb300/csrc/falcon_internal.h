@@ -55,11 +55,16 @@ static_assert(sizeof(Control) == 64, "control block is 64 bytes");
 constexpr size_t kControlBytes = 256;   // control block region (keeps flags 256-aligned)
 
 // Workspace words of a job: compression keeps two per chunk (the analysis results and the
-// dense-row mask) and then one per 64-chunk tile (the tile's record offset); decompression
-// uses the tile offsets only, in the first words.
+// dense-row mask), then one per 64-chunk tile and one per 4096-chunk group (the sums of their
+// record sizes, which the analysis adds up); decompression keeps the record offset of each tile
+// in the first words.
 constexpr uint64_t kTile = 64;
+constexpr uint64_t kGroup = 4096;
 __host__ __device__ constexpr uint64_t tile_count(uint64_t nchunks) { return (nchunks + kTile - 1) / kTile; }
-__host__ __device__ constexpr uint64_t workspace_words(uint64_t nchunks) { return 2 * nchunks + tile_count(nchunks); }
+__host__ __device__ constexpr uint64_t group_count(uint64_t nchunks) { return (nchunks + kGroup - 1) / kGroup; }
+__host__ __device__ constexpr uint64_t workspace_words(uint64_t nchunks) {
+    return 2 * nchunks + tile_count(nchunks) + group_count(nchunks);
+}
 
 cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single,
                             uint64_t total_chunks, Control *ctl, cudaStream_t stream);

@@ -12,7 +12,7 @@ namespace {
 // describes, for FALCON_NOALLOC_MAX_CHUNKS chunks
 constexpr size_t kWords = falcon::workspace_words(FALCON_NOALLOC_MAX_CHUNKS);
 constexpr size_t kScratchBytes = falcon::kControlBytes + (8 * kWords + 255) / 256 * 256;
-static_assert(kScratchBytes == 1057024, "scratch size as documented in falcon.h");
+static_assert(kScratchBytes == 1057280, "scratch size as documented in falcon.h");
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 

@@ -280,6 +280,14 @@ struct falcon_server {
         if (cudaMemcpyAsync(d_jobs(s), s.h_jobs, sizeof(Job) * (size_t)count, cudaMemcpyHostToDevice, cs) != cudaSuccess)
             return FALCON_ERR_CUDA;
         if (cudaMemsetAsync(s.d_area, 0, kControlBytes + 16 * (size_t)count, cs) != cudaSuccess) return FALCON_ERR_CUDA;
+        if (g.op == FALCON_COMPRESS)            // the analysis adds record sizes to per-tile and per-group sums
+            for (const Request &r : g.reqs) {
+                if (r.nchunks == 0) continue;
+                auto *words = reinterpret_cast<unsigned long long *>(d_base + r.dev_off + r.in_span() + r.out_span());
+                if (cudaMemsetAsync(words + 2 * r.nchunks, 0, 8 * (tile_count(r.nchunks) + group_count(r.nchunks)),
+                                    cs) != cudaSuccess)
+                    return FALCON_ERR_CUDA;
+            }
         Job dummy{};
         auto *ctl = reinterpret_cast<Control *>(s.d_area);
         const cudaError_t e = g.op == FALCON_COMPRESS ? launch_compress(d_jobs(s), count, dummy, total, ctl, cs)

@@ -68,4 +68,6 @@ def test_stream_info_parses_oracle_streams(falcon_lib, oracle):
 def test_workspace_bytes(falcon_lib):
     assert falcon_lib.workspace_bytes(0) == 256
     assert falcon_lib.workspace_bytes(1) == 512
-    assert falcon_lib.workspace_bytes(65536) == 256 + 8 * (2 * 65536 + 1024)
+    # two words per chunk, one per 64-chunk tile and one per 4096-chunk group, 256-byte granules
+    words = 2 * 65536 + 1024 + 16
+    assert falcon_lib.workspace_bytes(65536) == 256 + (8 * words + 255) // 256 * 256
