@@ -43,6 +43,13 @@
  *       (in FP64), round trip and decode are fl32((float)g / (float)10^alpha).
  *   R16 block sizes: 2 <= B <= 1025 (Sec. 3.3's n = 64k + 1 with the implementation's
  *       n = 1025 as the largest chunk).
+ *   R18 FP16 (half precision; Sec. 2.1 says the method extends to other precisions and
+ *       fixes nothing more): alpha <= 4 (10^4 is the largest power of ten exact in binary16),
+ *       beta <= 3 (10^3 < 2^11 <= 10^4), mu = |x| * 2^-10 (the 11-bit significand's unit, as
+ *       2^-52 and 2^-23 are for FP64 and FP32), x = v * 10^alpha exact (in FP64); the round
+ *       trip and the decode are fl16(g / 10^alpha), correctly rounded (ties to even); the
+ *       Case-2 sentinels are (5, 4); zigzag and deltas are modulo 2^16; z_1 takes 2 bytes and
+ *       w <= 16.  -0, NaN, +-inf and subnormals are exceptions (R1).
  *   R17 the ablation variants of Sec. 5.4.2 (Fig. 12b) change one step each and keep the
  *       record layout, so the one decoder reads all of them:
  *         Fal._Sparse / Fal._Dense: every row of M^T stored sparse / dense;
@@ -52,10 +59,10 @@
  *         chunk's Case decision (Eq. 4) and the R6 round-trip check are unchanged.
  *
  * Stream layout (little-endian):
- *   0  "FLCN"  4  version=1 (u8)  5  dtype (u8: 0=f64, 1=f32)  6  reserved u16 = 0
+ *   0  "FLCN"  4  version=1 (u8)  5  dtype (u8: 0=f64, 1=f32, 2=f16)  6  reserved u16 = 0
  *   8  block_size u32   12 reserved u32 = 0   16 n u64   24 num_chunks u64
  *   32 u32 size[num_chunks]   then the chunk records, concatenated.
- * Chunk record: [alpha_max u8][beta_hat_max u8][z_1: 8 B (f32: 4 B)][w u8]
+ * Chunk record: [alpha_max u8][beta_hat_max u8][z_1: 8 B (f32: 4 B, f16: 2 B)][w u8]
  *               [flags: ceil(w/8) B][row 1] ... [row w]
  */
 #include <stdint.h>
@@ -65,7 +72,12 @@
 #include <string.h>
 #include <math.h>
 
-enum { OR_F64 = 0, OR_F32 = 1 };
+enum { OR_F64 = 0, OR_F32 = 1, OR_F16 = 2 };
+
+static int dtype_ok(int dtype) { return dtype == OR_F64 || dtype == OR_F32 || dtype == OR_F16; }
+static size_t elem_size(int dtype) { return dtype == OR_F64 ? 8 : (dtype == OR_F32 ? 4 : 2); }
+/* bits per value = bit planes of M^T (64 / 32 / 16); z_1 takes width / 8 bytes (R7) */
+static int width_of(int dtype) { return 8 * (int)elem_size(dtype); }
 enum { OR_OK = 0, OR_ERR_INVALID = 1, OR_ERR_CAPACITY = 2, OR_ERR_CORRUPT = 3 };
 
 #define OR_HEADER_BYTES 32u
@@ -238,6 +250,132 @@ void oracle_dp_elf_f32(float v, int *alpha, int *beta)
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* FP16 (R18).  Values are binary16 bit patterns (uint16_t); arithmetic on them is done   */
+/* exactly on integers and in FP64, and every binary16 result is one correctly rounded   */
+/* (ties to even) conversion of an exact value.                                         */
+/* ------------------------------------------------------------------------------------ */
+/* exact value of a binary16 pattern */
+double oracle_half_to_double(uint16_t u)
+{
+    const int sign = u >> 15, e = (u >> 10) & 0x1F;
+    const int m = u & 0x3FF;
+    double v;
+    if (e == 0x1F) v = m ? NAN : INFINITY;
+    else if (e == 0) v = ldexp((double)m, -24);                 /* subnormal or zero */
+    else v = ldexp((double)(1024 + m), e - 25);
+    return sign ? -v : v;
+}
+
+/* binary16 nearest to (-1)^neg * num / den * 2^e2 (num, den > 0; ties to even; overflow to
+   infinity, gradual underflow).  The exponent is found first (2^e <= |value| < 2^(e+1)); the
+   value is then divided by its quantum 2^(max(e, -14) - 10) and rounded. */
+static uint16_t half_from_ratio(int neg, uint64_t num, uint64_t den, int e2)
+{
+    const uint16_t sbit = neg ? 0x8000u : 0u;
+    if (num == 0) return sbit;
+    uint64_t n = num, d = den;
+    int e = e2;
+    while (n < d) { n <<= 1; --e; }
+    while (n >= 2 * d) { d <<= 1; ++e; }
+    if (e > 15) return sbit | 0x7C00u;                          /* beyond the largest finite */
+    const int qe = (e < -14 ? -14 : e) - 10;                    /* quantum 2^qe */
+    uint64_t a = num, b = den;
+    if (e2 - qe >= 0) a <<= (e2 - qe); else b <<= (qe - e2);
+    uint64_t k = a / b;
+    const uint64_t r = a % b;
+    if (2 * r > b || (2 * r == b && (k & 1))) ++k;
+    if (qe == -24) return sbit | (uint16_t)k;                   /* subnormal range; k = 1024 is 2^-14 */
+    int ee = e;
+    if (k == 2048) { k = 1024; ++ee; }
+    if (ee > 15) return sbit | 0x7C00u;
+    return sbit | (uint16_t)((ee + 15) << 10) | (uint16_t)(k - 1024);
+}
+
+/* fl16(10^k) */
+uint16_t oracle_pow10_f16(int k)
+{
+    if (k > 4) return 0x7C00u;                                  /* 10^5 > 65504 */
+    uint64_t p = 1;
+    for (int i = 0; i < (k < 0 ? -k : k); ++i) p *= 10;
+    return k >= 0 ? half_from_ratio(0, p, 1, 0) : half_from_ratio(0, 1, p, 0);
+}
+
+/* fl16(g / 10^a), g an integer, 0 <= a <= 4: Case-1 round trip and decode (R18) */
+uint16_t oracle_f16_div_pow10(int32_t g, int a)
+{
+    uint64_t p = 1;
+    for (int i = 0; i < a; ++i) p *= 10;
+    const int neg = g < 0;
+    const uint64_t mag = neg ? (uint64_t)(-(int64_t)g) : (uint64_t)g;
+    return half_from_ratio(neg, mag, p, 0);
+}
+
+/* R1 for binary16 */
+int oracle_is_special_f16(uint16_t u)
+{
+    const unsigned e = (u >> 10) & 0x1F;
+    if (e == 0x1F) return 1;                                    /* NaN, +-inf */
+    if (e == 0 && (u & 0x3FF) != 0) return 1;                   /* subnormal */
+    if (u == 0x8000u) return 1;                                 /* -0 */
+    return 0;
+}
+
+/* R3 for binary16: the largest k with |v| >= fl16(10^k); |v| normal, finite */
+int oracle_floor_log10_f16(uint16_t u)
+{
+    const double a = fabs(oracle_half_to_double(u));
+    int k = (int)floor(log10(a));
+    while (k > -9 && a < oracle_half_to_double(oracle_pow10_f16(k))) --k;
+    while (k < 4 && a >= oracle_half_to_double(oracle_pow10_f16(k + 1))) ++k;
+    return k;
+}
+
+/* Alg. 2 for binary16 (R18): alpha <= 4, beta <= 3, mu = |x| * 2^-10, x exact in FP64 */
+void oracle_dp_ds_f16(uint16_t v, int *alpha, int *beta)
+{
+    if (oracle_is_special_f16(v)) { *alpha = 5; *beta = 4; return; }
+    if (v == 0) { *alpha = 0; *beta = 0; return; }
+    const double vd = oracle_half_to_double(v);
+    int a = 0;
+    int b = a + oracle_floor_log10_f16(v) + 1;
+    while (b <= 3 && a <= 4) {
+        double x = vd * oracle_half_to_double(oracle_pow10_f16(a));  /* exact */
+        double r = round(x);
+        if (fabs(x - r) <= fabs(x) * 0x1p-10) {
+            if (oracle_f16_div_pow10((int32_t)r, a) != v) { a = 5; b = 4; }
+            break;
+        }
+        a = a + 1;
+        b = b + 1;
+    }
+    *alpha = a;
+    *beta = b;
+}
+
+/* Fal._Elf's decimal place for binary16 (R17): the first i with v (x) 10^i integral, the
+   product rounded to binary16 (the IEEE multiply of the format) */
+void oracle_dp_elf_f16(uint16_t v, int *alpha, int *beta)
+{
+    if (oracle_is_special_f16(v)) { *alpha = 5; *beta = 4; return; }
+    if (v == 0) { *alpha = 0; *beta = 0; return; }
+    const int e = (v >> 10) & 0x1F;
+    const uint64_t sig = 1024u + (v & 0x3FFu);                  /* |v| = sig * 2^(e - 25) */
+    int a = 0;
+    int b = a + oracle_floor_log10_f16(v) + 1;
+    while (b <= 3 && a <= 4) {
+        uint64_t p = 1;
+        for (int i = 0; i < a; ++i) p *= 10;
+        const double x = oracle_half_to_double(half_from_ratio(0, sig * p, 1, e - 25));
+        if (x == floor(x)) break;
+        a = a + 1;
+        b = b + 1;
+    }
+    if (a > 4 || b > 3) { a = 5; b = 4; }
+    *alpha = a;
+    *beta = b;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Zigzag (Eq. 5): Zigzag(x) = (x << 1) xor (x >> 63), arithmetic shift (R7).           */
 /* ------------------------------------------------------------------------------------ */
 uint64_t oracle_zigzag64(uint64_t x)
@@ -255,6 +393,14 @@ uint32_t oracle_zigzag32(uint32_t x)
 uint32_t oracle_unzigzag32(uint32_t z)
 {
     return (z >> 1) ^ (0u - (z & 1u));
+}
+uint16_t oracle_zigzag16(uint16_t x)
+{
+    return (uint16_t)((uint16_t)(x << 1) ^ (uint16_t)((int16_t)x >> 15));
+}
+uint16_t oracle_unzigzag16(uint16_t z)
+{
+    return (uint16_t)((z >> 1) ^ (uint16_t)(0u - (z & 1u)));
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -311,6 +457,47 @@ static int chunk_transform_with(const void *vals, uint32_t m, int dtype, int elf
                 g[i] = oracle_zigzag64(bits64(v[i])); /* g_i = Zigzag(BinLong(v_i)) */
             alpha_max = 23;
             beta_hat = 16;
+        }
+        *alpha_max_out = alpha_max;
+        *beta_hat_out = beta_hat;
+        *case1_out = case1;
+    } else if (dtype == OR_F16) {
+        const uint16_t *v = (const uint16_t *)vals;             /* binary16 patterns (R18) */
+        int alpha_max = 0;
+        int any_exception = 0;
+        for (uint32_t i = 0; i < m; ++i) {
+            int a, b;
+            if (elf) oracle_dp_elf_f16(v[i], &a, &b);
+            else oracle_dp_ds_f16(v[i], &a, &b);
+            if (a > alpha_max) alpha_max = a;
+            if (a > 4 || b > 3) any_exception = 1;
+        }
+        int beta_hat = 4;
+        if (alpha_max <= 4) {
+            uint16_t v_max = 0;                                 /* |v| orders as its pattern */
+            for (uint32_t i = 0; i < m; ++i) {
+                uint16_t av = v[i] & 0x7FFFu;
+                if (av > v_max) v_max = av;
+            }
+            beta_hat = (v_max == 0) ? 0 : alpha_max + oracle_floor_log10_f16(v_max) + 1;
+        }
+        int case1 = (alpha_max <= 4 && beta_hat <= 3);
+        if (any_exception) case1 = 0;
+        if (case1) {
+            const double p = oracle_half_to_double(oracle_pow10_f16(alpha_max));
+            for (uint32_t i = 0; i < m; ++i) {
+                double x = oracle_half_to_double(v[i]) * p;     /* exact */
+                int32_t gi = (int32_t)llround(x);
+                g[i] = (uint64_t)(uint16_t)gi;
+                if (oracle_f16_div_pow10(gi, alpha_max) != v[i]) ++r6_firings;
+            }
+            if (r6_firings) case1 = 0;
+        }
+        if (!case1) {
+            for (uint32_t i = 0; i < m; ++i)
+                g[i] = (uint64_t)oracle_zigzag16(v[i]);
+            alpha_max = 5;
+            beta_hat = 4;
         }
         *alpha_max_out = alpha_max;
         *beta_hat_out = beta_hat;
@@ -376,7 +563,7 @@ int oracle_chunk_transform_elf(const void *vals, uint32_t m, int dtype,
     return chunk_transform_with(vals, m, dtype, 1, alpha_max_out, beta_hat_out, case1_out, g);
 }
 
-/* Eq. 5: z_1 = g_1, z_i = Zigzag(g_i - g_{i-1}) for i > 1 (modulo 2^64 / 2^32). */
+/* Eq. 5: z_1 = g_1, z_i = Zigzag(g_i - g_{i-1}) for i > 1 (modulo 2^64 / 2^32 / 2^16). */
 void oracle_delta_zigzag(const uint64_t *g, uint32_t m, int dtype, uint64_t *z)
 {
     for (uint32_t i = 0; i < m; ++i) {
@@ -384,6 +571,8 @@ void oracle_delta_zigzag(const uint64_t *g, uint32_t m, int dtype, uint64_t *z)
             z[i] = g[0];
         } else if (dtype == OR_F64) {
             z[i] = oracle_zigzag64(g[i] - g[i - 1]);
+        } else if (dtype == OR_F16) {
+            z[i] = (uint64_t)oracle_zigzag16((uint16_t)((uint16_t)g[i] - (uint16_t)g[i - 1]));
         } else {
             z[i] = (uint64_t)oracle_zigzag32((uint32_t)g[i] - (uint32_t)g[i - 1]);
         }
@@ -414,8 +603,8 @@ enum { OR_STORE_ADAPTIVE = 0, OR_STORE_SPARSE = 1, OR_STORE_DENSE = 2 };
 size_t oracle_encode_z_storage(const uint64_t *z, uint32_t m, int dtype, int alpha_max, int beta_hat,
                                int storage, uint8_t *out, size_t cap)
 {
-    const int width = (dtype == OR_F64) ? 64 : 32;
-    const int z1_bytes = (dtype == OR_F64) ? 8 : 4;
+    const int width = width_of(dtype);
+    const int z1_bytes = width / 8;
     const uint32_t cols = chunk_cols(m);
     const uint32_t row_bytes = cols / 8;
     const uint32_t bitmap_bytes = cols / 64;
@@ -518,14 +707,14 @@ static uint64_t num_chunks_of(uint64_t n, uint32_t block) { return (n + block - 
 
 static size_t record_bound(uint32_t m, int dtype)
 {
-    const int width = (dtype == OR_F64) ? 64 : 32;
-    const int z1_bytes = (dtype == OR_F64) ? 8 : 4;
+    const int width = width_of(dtype);
+    const int z1_bytes = width / 8;
     return 2 + (size_t)z1_bytes + 1 + (size_t)(width / 8) + (size_t)width * (chunk_cols(m) / 8);
 }
 
 size_t oracle_bound(uint64_t n, int dtype, uint32_t block)
 {
-    if ((dtype != OR_F64 && dtype != OR_F32) || block < 2 || block > OR_MAX_BLOCK) return 0;
+    if (!dtype_ok(dtype) || block < 2 || block > OR_MAX_BLOCK) return 0;
     uint64_t nc = num_chunks_of(n, block);
     size_t total = OR_HEADER_BYTES + 4 * (size_t)nc;
     if (nc == 0) return total;
@@ -540,7 +729,7 @@ size_t oracle_bound_variant(uint64_t n, int dtype, uint32_t block, int variant)
 {
     size_t total = oracle_bound(n, dtype, block);
     if (total == 0 || variant != 1) return total;          /* 1 = Fal._Sparse */
-    const int width = (dtype == OR_F64) ? 64 : 32;
+    const int width = width_of(dtype);
     const uint64_t nc = num_chunks_of(n, block);
     if (nc == 0) return total;
     total += (size_t)(nc - 1) * (size_t)width * (chunk_cols(block) / 64);
@@ -568,9 +757,9 @@ static void put_header(uint8_t *out, uint64_t n, int dtype, uint32_t block, uint
 int oracle_compress_variant(const void *in, uint64_t n, int dtype, uint32_t block, int variant,
                             uint8_t *out, size_t cap, size_t *out_bytes)
 {
-    if ((dtype != OR_F64 && dtype != OR_F32) || block < 2 || block > OR_MAX_BLOCK) return OR_ERR_INVALID;
+    if (!dtype_ok(dtype) || block < 2 || block > OR_MAX_BLOCK) return OR_ERR_INVALID;
     if (variant < OR_VARIANT_FALCON || variant > OR_VARIANT_ELF) return OR_ERR_INVALID;
-    const size_t s = (dtype == OR_F64) ? 8 : 4;
+    const size_t s = elem_size(dtype);
     const uint64_t nc = num_chunks_of(n, block);
     const size_t data_start = OR_HEADER_BYTES + 4 * (size_t)nc;
     if (cap < data_start) return OR_ERR_CAPACITY;
@@ -605,7 +794,7 @@ int oracle_stream_info(const uint8_t *in, size_t in_bytes, uint64_t *n, int *dty
     uint32_t b = get_u32(in + 8);
     uint64_t nn = get_u64(in + 16);
     uint64_t nc = get_u64(in + 24);
-    if (dt != OR_F64 && dt != OR_F32) return OR_ERR_CORRUPT;
+    if (!dtype_ok(dt)) return OR_ERR_CORRUPT;
     if (b < 2 || b > OR_MAX_BLOCK) return OR_ERR_CORRUPT;
     if (nc != num_chunks_of(nn, b)) return OR_ERR_CORRUPT;
     *n = nn; *dtype = dt; *block = b; *num_chunks = nc;
@@ -615,8 +804,8 @@ int oracle_stream_info(const uint8_t *in, size_t in_bytes, uint64_t *n, int *dty
 /* Sec. 4: decode one record of m values. Returns OR_OK or OR_ERR_CORRUPT. */
 int oracle_decode_chunk(const uint8_t *rec, size_t len, uint32_t m, int dtype, void *vals)
 {
-    const int width = (dtype == OR_F64) ? 64 : 32;
-    const int z1_bytes = (dtype == OR_F64) ? 8 : 4;
+    const int width = width_of(dtype);
+    const int z1_bytes = width / 8;
     const uint32_t cols = chunk_cols(m);
     const uint32_t row_bytes = cols / 8;
     const uint32_t bitmap_bytes = cols / 64;
@@ -685,6 +874,15 @@ int oracle_decode_chunk(const uint8_t *rec, size_t len, uint32_t m, int dtype, v
             if (case1) out[i] = (double)(int64_t)g / oracle_pow10_f64(alpha);
             else out[i] = from_bits64(oracle_unzigzag64(g));
         }
+    } else if (dtype == OR_F16) {
+        int case1 = (alpha <= 4 && beta_hat <= 3);                  /* R18 */
+        uint16_t *out = (uint16_t *)vals;
+        uint16_t g = (uint16_t)z[0];
+        for (uint32_t i = 0; i < m; ++i) {
+            if (i > 0) g = (uint16_t)(g + oracle_unzigzag16((uint16_t)z[i]));
+            if (case1) out[i] = oracle_f16_div_pow10((int16_t)g, alpha);
+            else out[i] = oracle_unzigzag16(g);
+        }
     } else {
         int case1 = (alpha <= 10 && beta_hat <= 7);
         float *out = (float *)vals;
@@ -707,7 +905,7 @@ int oracle_decompress(const uint8_t *in, size_t in_bytes, void *out, size_t out_
     uint32_t block;
     int st = oracle_stream_info(in, in_bytes, &n, &dtype, &block, &nc);
     if (st != OR_OK) return st;
-    const size_t s = (dtype == OR_F64) ? 8 : 4;
+    const size_t s = elem_size(dtype);
     if (n > out_cap_bytes / s) return OR_ERR_CAPACITY;
     size_t data_start = OR_HEADER_BYTES + 4 * (size_t)nc;
     if (nc > (in_bytes - OR_HEADER_BYTES) / 4 || data_start > in_bytes) return OR_ERR_CORRUPT;
@@ -747,7 +945,7 @@ typedef struct {
 static void *mt_comp_encode(void *arg)
 {
     mt_comp *t = (mt_comp *)arg;
-    const size_t s = (t->dtype == OR_F64) ? 8 : 4;
+    const size_t s = elem_size(t->dtype);
     size_t pos = 0;
     for (uint64_t c = t->c0; c < t->c1; ++c) {
         uint64_t first = c * t->block;
@@ -772,7 +970,7 @@ static void *mt_comp_place(void *arg)
 int oracle_compress_mt(const void *in, uint64_t n, int dtype, uint32_t block, int variant, int nthreads,
                        uint8_t *out, size_t cap, size_t *out_bytes)
 {
-    if ((dtype != OR_F64 && dtype != OR_F32) || block < 2 || block > OR_MAX_BLOCK) return OR_ERR_INVALID;
+    if (!dtype_ok(dtype) || block < 2 || block > OR_MAX_BLOCK) return OR_ERR_INVALID;
     if (variant < OR_VARIANT_FALCON || variant > OR_VARIANT_ELF || nthreads < 1) return OR_ERR_INVALID;
     const uint64_t nc = num_chunks_of(n, block);
     const size_t data_start = OR_HEADER_BYTES + 4 * (size_t)nc;
@@ -830,7 +1028,7 @@ typedef struct {
 static void *mt_dec_run(void *arg)
 {
     mt_dec *t = (mt_dec *)arg;
-    const size_t s = (t->dtype == OR_F64) ? 8 : 4;
+    const size_t s = elem_size(t->dtype);
     for (uint64_t c = t->c0; c < t->c1; ++c) {
         uint64_t first = c * t->block;
         uint32_t m = (uint32_t)((t->n - first) < t->block ? (t->n - first) : t->block);
@@ -849,7 +1047,7 @@ int oracle_decompress_mt(const uint8_t *in, size_t in_bytes, void *out, size_t o
     if (nthreads < 1) return OR_ERR_INVALID;
     int st = oracle_stream_info(in, in_bytes, &n, &dtype, &block, &nc);
     if (st != OR_OK) return st;
-    const size_t s = (dtype == OR_F64) ? 8 : 4;
+    const size_t s = elem_size(dtype);
     if (n > out_cap_bytes / s) return OR_ERR_CAPACITY;
     if (nc > (in_bytes - OR_HEADER_BYTES) / 4) return OR_ERR_CORRUPT;
     size_t *offs = (size_t *)malloc(sizeof(size_t) * (size_t)(nc + 1));

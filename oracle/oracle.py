@@ -22,7 +22,7 @@ _SRC = os.path.join(_HERE, "falcon_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
-F64, F32 = 0, 1
+F64, F32, F16 = 0, 1, 2
 OK, ERR_INVALID, ERR_CAPACITY, ERR_CORRUPT = 0, 1, 2, 3
 # codec variants: Falcon and the ablations of Sec. 5.4.2 (Fal._Sparse, Fal._Dense, Fal._Elf)
 FALCON, SPARSE, DENSE, ELF = 0, 1, 2, 3
@@ -78,6 +78,20 @@ def lib():
             for name in ("oracle_zigzag32", "oracle_unzigzag32"):
                 getattr(L, name).restype = c.c_uint32
                 getattr(L, name).argtypes = [c.c_uint32]
+            # binary16 (R18): values cross the boundary as their 16-bit patterns
+            for name in ("oracle_zigzag16", "oracle_unzigzag16"):
+                getattr(L, name).restype = c.c_uint16
+                getattr(L, name).argtypes = [c.c_uint16]
+            L.oracle_pow10_f16.restype = c.c_uint16
+            L.oracle_pow10_f16.argtypes = [c.c_int]
+            L.oracle_f16_div_pow10.restype = c.c_uint16
+            L.oracle_f16_div_pow10.argtypes = [c.c_int32, c.c_int]
+            L.oracle_half_to_double.restype = c.c_double
+            L.oracle_half_to_double.argtypes = [c.c_uint16]
+            L.oracle_is_special_f16.argtypes = [c.c_uint16]
+            L.oracle_floor_log10_f16.argtypes = [c.c_uint16]
+            L.oracle_dp_ds_f16.argtypes = [c.c_uint16, c.POINTER(c.c_int), c.POINTER(c.c_int)]
+            L.oracle_dp_elf_f16.argtypes = [c.c_uint16, c.POINTER(c.c_int), c.POINTER(c.c_int)]
             L.oracle_chunk_transform.argtypes = [c.c_void_p, c.c_uint32, c.c_int,
                                                  c.POINTER(c.c_int), c.POINTER(c.c_int),
                                                  c.POINTER(c.c_int), c.c_void_p]
@@ -110,7 +124,20 @@ def _dtype_code(arr: np.ndarray) -> int:
         return F64
     if arr.dtype == np.float32:
         return F32
+    if arr.dtype == np.float16:
+        return F16
     raise TypeError(f"unsupported dtype {arr.dtype}")
+
+
+def _np_dtype(code: int):
+    return {F64: np.float64, F32: np.float32, F16: np.float16}[code]
+
+
+def _h(v) -> int:
+    """The binary16 pattern of v (a float16 or its uint16 pattern)."""
+    if isinstance(v, (int, np.integer)) and not isinstance(v, bool):
+        return int(v) & 0xFFFF
+    return int(np.array(v, dtype=np.float16).view(np.uint16))
 
 
 def _ptr(a: np.ndarray) -> int:
@@ -120,7 +147,18 @@ def _ptr(a: np.ndarray) -> int:
 # ----------------------------------------------------------------------------- scalar steps
 def pow10(k: int, dtype=np.float64):
     L = lib()
+    if dtype == np.float16:
+        return np.array(L.oracle_pow10_f16(k), dtype=np.uint16).view(np.float16)[()]
     return L.oracle_pow10_f64(k) if dtype == np.float64 else np.float32(L.oracle_pow10_f32(k))
+
+
+def f16_div_pow10(g: int, a: int) -> int:
+    """fl16(g / 10^a) as a binary16 pattern (R18's Case-1 round trip and decode)."""
+    return lib().oracle_f16_div_pow10(g, a)
+
+
+def half_to_double(u: int) -> float:
+    return lib().oracle_half_to_double(u & 0xFFFF)
 
 
 def dp_ds(v, dtype=np.float64):
@@ -129,6 +167,8 @@ def dp_ds(v, dtype=np.float64):
     a, b = ctypes.c_int(), ctypes.c_int()
     if dtype == np.float64:
         L.oracle_dp_ds_f64(float(v), ctypes.byref(a), ctypes.byref(b))
+    elif dtype == np.float16:
+        L.oracle_dp_ds_f16(_h(v), ctypes.byref(a), ctypes.byref(b))
     else:
         L.oracle_dp_ds_f32(float(np.float32(v)), ctypes.byref(a), ctypes.byref(b))
     return a.value, b.value
@@ -140,6 +180,8 @@ def dp_elf(v, dtype=np.float64):
     a, b = ctypes.c_int(), ctypes.c_int()
     if dtype == np.float64:
         L.oracle_dp_elf_f64(float(v), ctypes.byref(a), ctypes.byref(b))
+    elif dtype == np.float16:
+        L.oracle_dp_elf_f16(_h(v), ctypes.byref(a), ctypes.byref(b))
     else:
         L.oracle_dp_elf_f32(float(np.float32(v)), ctypes.byref(a), ctypes.byref(b))
     return a.value, b.value
@@ -149,6 +191,8 @@ def floor_log10(v, dtype=np.float64) -> int:
     L = lib()
     if dtype == np.float64:
         return L.oracle_floor_log10_f64(float(v))
+    if dtype == np.float16:
+        return L.oracle_floor_log10_f16(_h(v))
     return L.oracle_floor_log10_f32(float(np.float32(v)))
 
 
@@ -156,6 +200,8 @@ def is_special(v, dtype=np.float64) -> bool:
     L = lib()
     if dtype == np.float64:
         return bool(L.oracle_is_special_f64(float(v)))
+    if dtype == np.float16:
+        return bool(L.oracle_is_special_f16(_h(v)))
     return bool(L.oracle_is_special_f32(float(np.float32(v))))
 
 
@@ -173,6 +219,14 @@ def zigzag32(x: int) -> int:
 
 def unzigzag32(z: int) -> int:
     return lib().oracle_unzigzag32(z & 0xFFFFFFFF)
+
+
+def zigzag16(x: int) -> int:
+    return lib().oracle_zigzag16(x & 0xFFFF)
+
+
+def unzigzag16(z: int) -> int:
+    return lib().oracle_unzigzag16(z & 0xFFFF)
 
 
 # ----------------------------------------------------------------------------- chunk steps
@@ -218,8 +272,8 @@ def encode_chunk(vals: np.ndarray) -> bytes:
 def decode_chunk(rec: bytes, m: int, dtype=np.float64) -> np.ndarray:
     buf = np.frombuffer(rec, dtype=np.uint8).copy()
     out = np.zeros(max(m, 1), dtype=dtype)
-    st = lib().oracle_decode_chunk(_ptr(buf), len(buf), m, F64 if dtype == np.float64 else F32,
-                                   _ptr(out))
+    code = {np.dtype(np.float64): F64, np.dtype(np.float32): F32, np.dtype(np.float16): F16}[np.dtype(dtype)]
+    st = lib().oracle_decode_chunk(_ptr(buf), len(buf), m, code, _ptr(out))
     if st != OK:
         raise ValueError(f"oracle_decode_chunk status {st}")
     return out[:m]
@@ -275,8 +329,8 @@ def decompress_status(stream: bytes, threads: int = 1):
         n, dt, _, _ = stream_info(stream)
     except ValueError:
         return ERR_CORRUPT, None
-    dtype = np.float64 if dt == F64 else np.float32
-    s = 8 if dt == F64 else 4
+    dtype = _np_dtype(dt)
+    s = np.dtype(dtype).itemsize
     if n > (1 << 34):
         return ERR_CORRUPT, None
     out = np.zeros(max(n, 1), dtype=dtype)
