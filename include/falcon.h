@@ -56,7 +56,7 @@ extern "C" {
 #define FALCON_HEADER_BYTES 32
 #define FALCON_MAX_BLOCK 1025
 
-typedef enum { FALCON_F64 = 0, FALCON_F32 = 1 } falcon_dtype;
+typedef enum { FALCON_F64 = 0, FALCON_F32 = 1, FALCON_F16 = 2 } falcon_dtype;
 
 typedef enum {
     FALCON_OK = 0,
@@ -198,7 +198,7 @@ typedef struct {
     uint64_t n;             /* compress: number of values (decompress: taken from h_header) */
     uint64_t in_bytes;      /* decompress: stream length in bytes (compress: ignored) */
     uint64_t out_capacity;  /* bytes available at d_out */
-    int32_t dtype;          /* compress: FALCON_F64 or FALCON_F32 (decompress: ignored) */
+    int32_t dtype;          /* compress: FALCON_F64, FALCON_F32 or FALCON_F16 (decompress: ignored) */
     uint32_t block_size;    /* compress: values per chunk (decompress: ignored) */
     const void *h_header;   /* decompress: HOST copy of the stream's first 32 bytes; compress: NULL */
 } falcon_series;

@@ -23,7 +23,7 @@ namespace {
 constexpr size_t kResultOffset = 64;     // plain API: 2 x u64 result inside the control block
 
 uint64_t num_chunks(uint64_t n, uint32_t block) { return (n + block - 1) / block; }
-size_t elem_bytes(int dtype) { return dtype == FALCON_F64 ? 8 : 4; }
+size_t elem_bytes(int dtype) { return dtype_bytes(dtype); }
 
 int check_block(uint32_t block) {
     if (block < 2 || block > kMaxBlock) return FALCON_ERR_INVALID;
@@ -31,7 +31,7 @@ int check_block(uint32_t block) {
 }
 
 size_t record_bound(uint64_t m, int dtype) {
-    const size_t W = dtype == FALCON_F64 ? 64 : 32;
+    const size_t W = 8 * dtype_bytes(dtype);
     const size_t cols = m <= 1 ? 0 : ((m - 1 + 63) / 64) * 64;
     return 2 + W / 8 + 1 + W / 8 + W * (cols / 8);
 }
@@ -79,7 +79,7 @@ int parse_header(const uint8_t *h, size_t len, Header *out) {
     std::memcpy(&r.block, h + 8, 4);
     std::memcpy(&r.n, h + 16, 8);
     std::memcpy(&r.nchunks, h + 24, 8);
-    if (r.dtype != FALCON_F64 && r.dtype != FALCON_F32) return FALCON_ERR_CORRUPT;
+    if (!dtype_valid(r.dtype)) return FALCON_ERR_CORRUPT;
     if (r.block < 2 || r.block > kMaxBlock) return FALCON_ERR_CORRUPT;
     if (r.nchunks != num_chunks(r.n, r.block)) return FALCON_ERR_CORRUPT;
     *out = r;
@@ -91,7 +91,7 @@ int parse_header(const uint8_t *h, size_t len, Header *out) {
 // Argument checks shared by every compression entry point (falcon_internal.h).
 int falcon::compress_args(const void *d_in, uint64_t n, int dtype, uint32_t block, void *d_out,
                           size_t out_capacity) {
-    if (dtype != FALCON_F64 && dtype != FALCON_F32) return FALCON_ERR_INVALID;
+    if (!dtype_valid(dtype)) return FALCON_ERR_INVALID;
     int st = check_block(block);
     if (st) return st;
     if (!d_out || (n > 0 && !d_in)) return FALCON_ERR_INVALID;
@@ -176,7 +176,7 @@ const char *falcon_status_string(int status) {
 }
 
 size_t falcon_bound(uint64_t n, int dtype, uint32_t block_size) {
-    if ((dtype != FALCON_F64 && dtype != FALCON_F32) || block_size < 2 || block_size > kMaxBlock) return 0;
+    if (!dtype_valid(dtype) || block_size < 2 || block_size > kMaxBlock) return 0;
     const uint64_t nc = num_chunks(n, block_size);
     size_t total = FALCON_HEADER_BYTES + 4 * (size_t)nc;
     if (nc == 0) return total;
@@ -238,7 +238,7 @@ size_t falcon_variant_bound(uint64_t n, int dtype, uint32_t block_size, int vari
     if (total == 0 || variant != FALCON_VARIANT_SPARSE) return total;
     const uint64_t nc = num_chunks(n, block_size);
     if (nc == 0) return total;
-    const size_t W = dtype == FALCON_F64 ? 64 : 32;
+    const size_t W = 8 * dtype_bytes(dtype);
     auto cols = [](uint64_t m) -> size_t { return m <= 1 ? 0 : ((m - 1 + 63) / 64) * 64; };
     total += (size_t)(nc - 1) * W * (cols(block_size) / 64);
     total += W * (cols(n - (nc - 1) * (uint64_t)block_size) / 64);

@@ -126,12 +126,12 @@ __device__ __forceinline__ uint32_t sparse_row(uint8_t *buf, uint32_t P, uint32_
 }
 
 // value k of this lane from the swizzled staging buffer
-template <bool F64>
-__device__ __forceinline__ typename Traits<F64>::U lane_value(const uint8_t *buf, int lane, int k) {
-    using U = typename Traits<F64>::U;
-    constexpr int UN = Traits<F64>::UNITS;
-    constexpr int PER = 16 / Traits<F64>::S;
-    return *reinterpret_cast<const U *>(buf + (lane * UN + ((k / PER) ^ (lane & 7))) * 16 + (k % PER) * Traits<F64>::S);
+template <int D>
+__device__ __forceinline__ typename Traits<D>::U lane_value(const uint8_t *buf, int lane, int k) {
+    using U = typename Traits<D>::U;
+    constexpr int UN = Traits<D>::UNITS;
+    constexpr int PER = 16 / Traits<D>::S;
+    return *reinterpret_cast<const U *>(buf + (lane * UN + unit_swizzle<D>(lane, k / PER)) * 16 + (k % PER) * Traits<D>::S);
 }
 
 // Every value of the chunk (the lane's 32 in v, value 1024 of a 1025-value chunk in vx)
@@ -139,15 +139,15 @@ __device__ __forceinline__ typename Traits<F64>::U lane_value(const uint8_t *buf
 // Every value of the chunk passes Alg. 2's test at a; the values are re-read from the staging
 // buffer (index >= m: not a value).  A failing decimal place usually fails on every lane's
 // first value already, so those 32 are tested first.
-template <bool F64>
-__device__ __forceinline__ bool all_pass(const uint8_t *buf, int lane, uint32_t m, typename Traits<F64>::U vx,
+template <int D>
+__device__ __forceinline__ bool all_pass(const uint8_t *buf, int lane, uint32_t m, typename Traits<D>::U vx,
                                          int a) {
     const bool has0 = 32u * lane < m;
-    if (!__all_sync(kFull, !has0 || q_test(lane_value<F64>(buf, lane, 0), a))) return false;
+    if (!__all_sync(kFull, !has0 || q_test(lane_value<D>(buf, lane, 0), a))) return false;
     bool ok = q_test(vx, a);
 #pragma unroll 4
     for (int k = 1; k < 32; ++k)
-        if (32u * lane + k < m) ok &= q_test(lane_value<F64>(buf, lane, k), a);
+        if (32u * lane + k < m) ok &= q_test(lane_value<D>(buf, lane, k), a);
     return __all_sync(kFull, ok);
 }
 
@@ -159,11 +159,11 @@ __device__ __forceinline__ bool all_pass(const uint8_t *buf, int lane, uint32_t 
 // is a lower bound, and for most chunks the answer: one all-value test confirms it.
 // Otherwise the answer lies above it (test atop, then bisect).  Out of line, reading the
 // staged values: few chunks get here, and the hot path of the others stays small.
-template <bool F64>
-__device__ __noinline__ int search_alpha(const uint8_t *buf, int lane, uint32_t m, typename Traits<F64>::U vx,
+template <int D>
+__device__ __noinline__ int search_alpha(const uint8_t *buf, int lane, uint32_t m, typename Traits<D>::U vx,
                                          int atop) {
-    using U = typename Traits<F64>::U;
-    const U v0 = 32u * lane < m ? lane_value<F64>(buf, lane, 0) : (U)0;
+    using U = typename Traits<D>::U;
+    const U v0 = 32u * lane < m ? lane_value<D>(buf, lane, 0) : (U)0;
     if (!__all_sync(kFull, q_test(v0, atop))) return -1;
     int a0 = 0;
 #pragma unroll 1
@@ -174,7 +174,7 @@ __device__ __noinline__ int search_alpha(const uint8_t *buf, int lane, uint32_t 
     int a = lb;
 #pragma unroll 1
     for (;;) {
-        const bool ok = all_pass<F64>(buf, lane, m, vx, a);
+        const bool ok = all_pass<D>(buf, lane, m, vx, a);
         if (ok) {
             hi = a;
             hi_ok = true;
@@ -187,13 +187,14 @@ __device__ __noinline__ int search_alpha(const uint8_t *buf, int lane, uint32_t 
     }
 }
 
-// FP32 chunks at beta_hat = 7 (R14): Alg. 2, value by value, stops at the first decimal place
-// where eps <= mu passes, and if the round trip fails there the value is an exception.  That
-// can happen below a value's own decimal place k only if |v| 10^k >= 2^23 / 1.5: with d / 10^k
-// its shortest decimal, v 10^a (a < k) lies at least 10^-(k-a) - |v| 10^a 2^-24 from every
-// integer, more than mu = |v 10^a| 2^-23 below that bound (checked exhaustively over every
-// decimal below it).  k <= alpha, so a value can stop early only if 3 |v| 10^alpha >= 2^23 (half
-// the bound, as a margin); only those values go through Alg. 2, and none when v_max is below.
+// FP32 chunks at beta_hat = 7 (R14) and FP16 chunks at beta_hat = 3 (R18): Alg. 2, value by
+// value, stops at the first decimal place where eps <= mu passes, and if the round trip fails
+// there the value is an exception.  That can happen below a value's own decimal place k only if
+// |v| 10^k >= 2^(p-1) / 1.5 (p = 24 or 11 significand bits): with d / 10^k its shortest decimal,
+// v 10^a (a < k) lies at least 10^-(k-a) - |v| 10^a 2^-p from every integer, more than
+// mu = |v 10^a| 2^-(p-1) below that bound (checked exhaustively over every decimal below it).
+// k <= alpha, so a value can stop early only if 3 |v| 10^alpha >= 2^(p-1) (half the bound, as a
+// margin); only those values go through Alg. 2, and none when v_max is below.
 __device__ __forceinline__ bool may_stop_early(uint32_t u, int a) {
     const uint32_t au = u & 0x7FFFFFFFu;
     if (au == 0) return false;
@@ -203,21 +204,34 @@ __device__ __forceinline__ bool may_stop_early(uint32_t u, int a) {
     const int s = 23 - E - a;                    // 3 m 5^a 2^(E+a) >= 2^23  <=>  p >= 2^s
     return s <= 0 || (s < 50 && p >= (1ull << s));
 }
+__device__ __forceinline__ bool may_stop_early(uint16_t u, int a) {
+    const uint32_t au = u & 0x7FFFu;
+    if (au == 0) return false;
+    if (au < 0x0400u) return true;
+    const int E = (int)(au >> 10) - 25;
+    const uint32_t p = 3u * ((au & 0x3FFu) | 0x400u) * (uint32_t)FALCON_POW5[a];     // < 2^22
+    const int s = 10 - E - a;                    // 3 m 5^a 2^(E+a) >= 2^10  <=>  p >= 2^s
+    return s <= 0 || (s < 32 && p >= (1u << s));
+}
+__device__ __forceinline__ int first_pass(uint32_t u, int atop) { return first_pass_f32(u, atop); }
+__device__ __forceinline__ int first_pass(uint16_t u, int atop) { return first_pass_f16(u, atop); }
 
 // True if some value of the chunk stops early (the chunk then takes Case 2); alpha is the
 // search's alpha_max, at which every value round-trips.
-__device__ __forceinline__ bool early_stop32(const uint8_t *buf, int lane, uint32_t m, const uint32_t (&v)[32],
-                                             uint32_t vx, bool has_vx, uint32_t vmax, int alpha) {
+template <int D>
+__device__ __forceinline__ bool early_stop(const uint8_t *buf, int lane, uint32_t m, const typename Traits<D>::U (&v)[32],
+                                           typename Traits<D>::U vx, bool has_vx, typename Traits<D>::U vmax,
+                                           int alpha) {
     if (!may_stop_early(vmax, alpha)) return false;
     uint32_t cand = 0;
 #pragma unroll
     for (int k = 0; k < 32; ++k) cand |= (uint32_t)(32u * lane + k < m && may_stop_early(v[k], alpha)) << k;
-    bool bad = has_vx && may_stop_early(vx, alpha) && first_pass_f32(vx, alpha) < 0;
+    bool bad = has_vx && may_stop_early(vx, alpha) && first_pass(vx, alpha) < 0;
 #pragma unroll 1
     while (cand) {
         const int k = __ffs(cand) - 1;
         cand &= cand - 1;
-        bad |= first_pass_f32(lane_value<false>(buf, lane, k), alpha) < 0;
+        bad |= first_pass(lane_value<D>(buf, lane, k), alpha) < 0;
     }
     return __any_sync(kFull, bad);
 }
@@ -249,19 +263,32 @@ __device__ __forceinline__ int elf_dp(uint32_t u) {
     }
     return -1;
 }
+__device__ __forceinline__ int elf_dp(uint16_t u) {      // binary16: products rounded to binary16
+    const uint32_t au = u & 0x7FFFu;
+    if (au == 0) return 0;
+    if (is_special(u)) return -1;
+    const int atop = min(4, 2 - floor_log10((uint16_t)au));
+    const float v = __half2float(__ushort_as_half(u));
+    for (int a = 0; a <= atop; ++a) {
+        // the product of two binary16 values is exact in FP32, so one rounding gives fl16
+        const float x = __half2float(__float2half_rn(v * (float)(FALCON_POW5[a] << a)));
+        if (x == floorf(x)) return a;
+    }
+    return -1;
+}
 
 // Fal._Elf: alpha_max = the largest of the values' Elf decimal places, then Eq. 4's bounds and
 // the R6 round trip at alpha_max, as for Falcon; -1 means Case 2.  Out of line (an ablation).
-template <bool F64>
-__device__ __noinline__ int alpha_elf(const uint8_t *buf, int lane, uint32_t m, typename Traits<F64>::U vx,
+template <int D>
+__device__ __noinline__ int alpha_elf(const uint8_t *buf, int lane, uint32_t m, typename Traits<D>::U vx,
                                       bool has_vx, int e_max) {
-    using T = Traits<F64>;
+    using T = Traits<D>;
     int amax = has_vx ? elf_dp(vx) : 0;
     bool bad = amax < 0;
 #pragma unroll 1
     for (int k = 0; k < 32; ++k) {
         if (32u * lane + k < m) {
-            const int a = elf_dp(lane_value<F64>(buf, lane, k));
+            const int a = elf_dp(lane_value<D>(buf, lane, k));
             bad |= a < 0;
             amax = a > amax ? a : amax;
         }
@@ -269,7 +296,7 @@ __device__ __noinline__ int alpha_elf(const uint8_t *buf, int lane, uint32_t m, 
     if (__any_sync(kFull, bad)) return -1;
     amax = (int)__reduce_max_sync(kFull, (uint32_t)amax);
     if (amax > T::A_MAX || amax + e_max + 1 > T::B_MAX) return -1;
-    return all_pass<F64>(buf, lane, m, vx, amax) ? amax : -1;
+    return all_pass<D>(buf, lane, m, vx, amax) ? amax : -1;
 }
 
 __device__ __forceinline__ void issue_chunk(const Job *jobs, int njobs, const Job &single, uint64_t t,
@@ -278,8 +305,9 @@ __device__ __forceinline__ void issue_chunk(const Job *jobs, int njobs, const Jo
     const uint64_t c = t - job.chunk_begin;
     const uint64_t first = c * (uint64_t)job.block;
     const uint32_t m = (uint32_t)((job.n - first) < job.block ? (job.n - first) : job.block);
-    if (job.dtype == 0) stage_values_async<true>(job.in + first * 8u, m, buf, lane);
-    else stage_values_async<false>(job.in + first * 4u, m, buf, lane);
+    if (job.dtype == 0) stage_values_async<kD64>(job.in + first * 8u, m, buf, lane);
+    else if (job.dtype == 1) stage_values_async<kD32>(job.in + first * 4u, m, buf, lane);
+    else stage_values_async<kD16>(job.in + first * 2u, m, buf, lane);
 }
 
 // Workspace words of a job (job.flags), written by the analysis launch:
@@ -295,11 +323,11 @@ __device__ __forceinline__ unsigned long long pack_meta(int alpha_byte, int beta
 
 // G (Eq. 4) and Z (Eq. 5) in place: v[k] becomes Z of column 32 lane + k, pad columns (R11)
 // are zero; alpha < 0 means Case 2.  Returns z_1 (every lane).
-template <bool F64>
-__device__ __forceinline__ typename Traits<F64>::U to_z(typename Traits<F64>::U (&v)[32],
-                                                        typename Traits<F64>::U vx, int alpha, uint32_t m,
+template <int D>
+__device__ __forceinline__ typename Traits<D>::U to_z(typename Traits<D>::U (&v)[32],
+                                                        typename Traits<D>::U vx, int alpha, uint32_t m,
                                                         int lane) {
-    using U = typename Traits<F64>::U;
+    using U = typename Traits<D>::U;
     U gx;
     if (alpha >= 0) {
 #pragma unroll
@@ -338,24 +366,24 @@ __device__ __forceinline__ uint32_t spread_nibble(uint32_t n) { return (n * 0x00
 // Launch 1, one chunk: everything up to the record size (see the file comment).  `next`
 // starts the copy of the warp's next chunk into buf; it is called once, as soon as the
 // staged values are no longer read (after the Case decision).
-template <bool F64, class Next>
+template <int D, class Next>
 __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, uint8_t *scratch, int lane,
                               Next &&next) {
-    using T = Traits<F64>;
+    using T = Traits<D>;
     using U = typename T::U;
-    constexpr U ABS = F64 ? (U)0x7FFFFFFFFFFFFFFFull : (U)0x7FFFFFFFu;
+    constexpr U ABS = (U)((U)~(U)0 >> 1);          // every bit but the sign (~ promotes uint16 to int)
     const uint32_t B = job.block;
     const uint64_t first = c * (uint64_t)B;
     const uint32_t m = (uint32_t)((job.n - first) < B ? (job.n - first) : B);
 
     // ---- 1. values, specials, maximum ------------------------------------------------------
     U v[32];
-    read_own<F64>(buf, lane, m, v);
+    read_own<D>(buf, lane, m, v);
     U vx = 0;                                   // value 1024 of a 1025-value chunk
-    if (m > 1024u && lane == 31) vx = read_elem<F64>(buf, 1024);
+    if (m > 1024u && lane == 31) vx = read_elem<D>(buf, 1024);
     bool sp;
     U vmax;
-    if constexpr (F64) {
+    if constexpr (D == 0) {
         // on 32-bit halves: special <=> exponent field all zeros (value != +0) or all ones
         uint32_t hmax = 0;
         bool s = false;
@@ -401,20 +429,20 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
             const int e_max = floor_log10(vmax);
             const int atop = min(T::A_MAX, T::B_MAX - 1 - e_max);
             if (job.variant == kVariantElf) {
-                alpha = alpha_elf<F64>(buf, lane, m, vx, m > 1024u && lane == 31, e_max);
+                alpha = alpha_elf<D>(buf, lane, m, vx, m > 1024u && lane == 31, e_max);
             } else if (atop >= 0) {
                 // quick rejection: Alg. 2 on the largest magnitude first.  The test reads
                 // only |v|, so it runs on vmax itself, the same in every lane.
                 bool fail;
-                if constexpr (F64) fail = !q_test(vmax, atop);
-                else fail = first_pass_f32(vmax, atop) < 0;
+                if constexpr (D == kD64) fail = !q_test(vmax, atop);
+                else fail = first_pass(vmax, atop) < 0;
                 if (!fail) {
-                    alpha = search_alpha<F64>(buf, lane, m, vx, atop);
-                    // FP32 (R14): below beta_hat = 7 no value can stop early (see
-                    // early_stop32), so Alg. 2 value by value gives the same alpha_max
-                    if constexpr (!F64) {
+                    alpha = search_alpha<D>(buf, lane, m, vx, atop);
+                    // FP32 (R14), FP16 (R18): below beta_hat = B_MAX no value can stop early
+                    // (see early_stop), so Alg. 2 value by value gives the same alpha_max
+                    if constexpr (D != kD64) {
                         if (alpha >= 0 && alpha + e_max + 1 == T::B_MAX &&
-                            early_stop32(buf, lane, m, v, vx, m > 1024u && lane == 31, vmax, alpha))
+                            early_stop<D>(buf, lane, m, v, vx, m > 1024u && lane == 31, vmax, alpha))
                             alpha = -1;
                     }
                 }
@@ -426,7 +454,7 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
     next();                                     // the staged values have been read
 
     // ---- 3. G, Z, w (from the ORs of 8-column groups that step 4 uses) -------------------------
-    (void)to_z<F64>(v, vx, alpha, m, lane);
+    (void)to_z<D>(v, vx, alpha, m, lane);
     U o[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -436,7 +464,7 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
         o[i] = x;
     }
     const U zor = warp_or_x((U)(o[0] | o[1] | o[2] | o[3]));
-    const int w = zor ? (T::W - (F64 ? __clzll((long long)zor) : __clz((int)zor))) : 0;
+    const int w = zor ? ((D == 0) ? 64 - __clzll((long long)zor) : 32 - __clz((int)zor)) : 0;
 
     // ---- 4. non-zero bytes per row, without forming the bit planes ----------------------------
     // This lane's four bytes of row p cover its columns 8i .. 8i + 7 (i = 0..3); byte i is
@@ -445,10 +473,11 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
     // planes 4g .. 4g + 3 in the bytes of packed[g].
     const uint32_t cols = chunk_cols(m);
     const uint32_t row_bytes = cols / 8u;
-    uint32_t packed[T::W / 4];
+    constexpr int PW = T::W < 32 ? 32 : T::W;  // planes the 32-bit words hold (FP16: 16 of them zero)
+    uint32_t packed[PW / 4];
     {
 #pragma unroll
-        for (int h = 0; h < T::W / 32; ++h) {
+        for (int h = 0; h < PW / 32; ++h) {
             const uint32_t o0 = (uint32_t)((uint64_t)o[0] >> (32 * h)), o1 = (uint32_t)((uint64_t)o[1] >> (32 * h));
             const uint32_t o2 = (uint32_t)((uint64_t)o[2] >> (32 * h)), o3 = (uint32_t)((uint64_t)o[3] >> (32 * h));
             const uint32_t x1 = o0 ^ o1, x2 = o2 ^ o3, c1 = o0 & o1, c2 = o2 & o3;
@@ -478,7 +507,7 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
         cost += sparse ? cols / 64u + nz : row_bytes;
         dense_lo = !sparse;
     }
-    if (F64 && lane + 32 < w) {                  // plane `lane + 32`
+    if (D == 0 && lane + 32 < w) {                  // plane `lane + 32`
         const uint32_t nz = scratch[lane + 32];
         const bool sparse = all_sparse || (!all_dense && (row_bytes - nz) > cols / 64u);
         cost += sparse ? cols / 64u + nz : row_bytes;
@@ -500,19 +529,26 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
 
 // Lane reads its 32 values (indices 32 lane + k) from global memory, 16 bytes at a time when
 // the chunk is whole and 16-byte aligned; indices >= m read as +0.
-template <bool F64>
-__device__ __forceinline__ void load_own(const uint8_t *src, int lane, uint32_t m, typename Traits<F64>::U (&v)[32]) {
-    using U = typename Traits<F64>::U;
-    constexpr int UN = Traits<F64>::UNITS;
+template <int D>
+__device__ __forceinline__ void load_own(const uint8_t *src, int lane, uint32_t m, typename Traits<D>::U (&v)[32]) {
+    using U = typename Traits<D>::U;
+    constexpr int UN = Traits<D>::UNITS;
     constexpr int PER = 32 / UN;
     if (m >= 1024u && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
         const uint4 *q4 = reinterpret_cast<const uint4 *>(src) + lane * UN;
 #pragma unroll
         for (int u = 0; u < UN; ++u) {
             const uint4 q = __ldg(q4 + u);
-            if constexpr (F64) {
+            if constexpr (D == kD64) {
                 v[PER * u + 0] = ((U)q.y << 32) | q.x;
                 v[PER * u + 1] = ((U)q.w << 32) | q.z;
+            } else if constexpr (D == kD16) {
+                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    v[PER * u + 2 * h] = (U)(w4[h] & 0xFFFFu);
+                    v[PER * u + 2 * h + 1] = (U)(w4[h] >> 16);
+                }
             } else {
                 v[PER * u + 0] = q.x;
                 v[PER * u + 1] = q.y;
@@ -535,7 +571,7 @@ __device__ __forceinline__ void prefetch_chunk(const Job *jobs, int njobs, const
     const Job &job = (jobs == nullptr) ? single : jobs[find_job(jobs, njobs, t)];
     const uint64_t first = (t - job.chunk_begin) * (uint64_t)job.block;
     const uint32_t m = (uint32_t)((job.n - first) < job.block ? (job.n - first) : job.block);
-    const uint32_t s = job.dtype == 0 ? 8u : 4u;
+    const uint32_t s = job.dtype == 0 ? 8u : (job.dtype == 1 ? 4u : 2u);
     const uint8_t *src = job.in + first * s;
     const uint8_t *end = src + (size_t)m * s;
     for (const uint8_t *q = src + 128u * (uint32_t)lane; q < end; q += 128u * 32u)
@@ -545,11 +581,11 @@ __device__ __forceinline__ void prefetch_chunk(const Job *jobs, int njobs, const
 // Launch 3, one chunk: G, Z and the plane words again (alpha and w from the analysis), then
 // the record at its offset.  meta / dense: the chunk's workspace words; size: its record size;
 // rel: its record offset relative to the first record.
-template <bool F64, bool kWide>
+template <int D, bool kWide>
 __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, unsigned long long meta,
                            unsigned long long dense, uint32_t size, uint64_t rel) {
     constexpr int kPlOff = EmitLayout<kWide>::kPlOff;
-    using T = Traits<F64>;
+    using T = Traits<D>;
     using U = typename T::U;
     const uint32_t B = job.block;
     const uint64_t first = c * (uint64_t)B;
@@ -564,15 +600,15 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     // ---- G, Z and the plane words in shared memory --------------------------------------------
     const uint8_t *src = job.in + first * T::S;
     U v[32];
-    load_own<F64>(src, lane, m, v);
+    load_own<D>(src, lane, m, v);
     U vx = 0;                                   // value 1024 of a 1025-value chunk
     if (m > 1024u && lane == 31) vx = __ldg(reinterpret_cast<const U *>(src) + 1024);
-    const U z1 = to_z<F64>(v, vx, alpha, m, lane);
+    const U z1 = to_z<D>(v, vx, alpha, m, lane);
     if (lane == 0) bulk_wait_read();             // the previous record has left the buffer
     __syncwarp();
     // half h of the values holds planes 32 h .. 32 h + 31 (the high half only when w > 32)
 #pragma unroll
-    for (int h = 0; h < (F64 ? 2 : 1); ++h) {
+    for (int h = 0; h < ((D == 0) ? 2 : 1); ++h) {
         if (h == 1 && w <= 32) break;
         uint32_t a[32];
 #pragma unroll
@@ -580,7 +616,7 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
         transpose32(a);
         uint8_t *dst = buf + kPlOff + (T::W - 1 - 32 * h) * 128 + 4 * lane;
 #pragma unroll
-        for (int p = 0; p < 32; ++p) *reinterpret_cast<uint32_t *>(dst - p * 128) = a[p];
+        for (int p = 0; p < (T::W < 32 ? T::W : 32); ++p) *reinterpret_cast<uint32_t *>(dst - p * 128) = a[p];
     }
     __syncwarp();
 
@@ -661,10 +697,10 @@ __device__ __forceinline__ const Job &job_of(const Job *jobs, int njobs, const J
 
 }  // namespace
 
-// The hot kernels come in three forms by dtype: kDt = 0 (every job FP64), 1 (every job FP32)
-// or 2 (either, per job: batches and the server).  A single-dtype form carries half the code,
-// which the instruction caches notice.
-constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2;
+// The hot kernels come in four forms by dtype: kDt = 0 (every job FP64), 1 (every job FP32),
+// 3 (every job FP16) or 2 (any, per job: batches and the server).  A single-dtype form carries
+// a third of the code, which the instruction caches notice.
+constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2, kDtF16 = 3;
 
 // Launch 1: analysis of every chunk (chunks by ticket; the next chunk is copied into
 // the warp's one value buffer while the current one is finished).
@@ -695,10 +731,12 @@ analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t tot
         };
         const Job &job = job_of(jobs, njobs, s_single, t);
         const uint64_t c = t - job.chunk_begin;
-        if constexpr (kDt == kDtF64) analyse_chunk<true>(job, c, wbase, scratch, lane, next);
-        else if constexpr (kDt == kDtF32) analyse_chunk<false>(job, c, wbase, scratch, lane, next);
-        else if (job.dtype == 0) analyse_chunk<true>(job, c, wbase, scratch, lane, next);
-        else analyse_chunk<false>(job, c, wbase, scratch, lane, next);
+        if constexpr (kDt == kDtF64) analyse_chunk<kD64>(job, c, wbase, scratch, lane, next);
+        else if constexpr (kDt == kDtF32) analyse_chunk<kD32>(job, c, wbase, scratch, lane, next);
+        else if constexpr (kDt == kDtF16) analyse_chunk<kD16>(job, c, wbase, scratch, lane, next);
+        else if (job.dtype == 0) analyse_chunk<kD64>(job, c, wbase, scratch, lane, next);
+        else if (job.dtype == 1) analyse_chunk<kD32>(job, c, wbase, scratch, lane, next);
+        else analyse_chunk<kD16>(job, c, wbase, scratch, lane, next);
         __syncwarp();
         if (tn >= total_chunks) break;
         t = tn;
@@ -803,10 +841,12 @@ __device__ __forceinline__ void emit_loop(const Job *__restrict__ jobs, int njob
         const uint64_t c = t - job.chunk_begin;
         const uint64_t rel = resolve_info(info);
         if (c == 0) finish_job(job, lane);
-        if constexpr (kDt == kDtF64) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
-        else if constexpr (kDt == kDtF32) emit_chunk<false, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
-        else if (job.dtype == 0) emit_chunk<true, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
-        else emit_chunk<false, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
+        if constexpr (kDt == kDtF64) emit_chunk<kD64, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
+        else if constexpr (kDt == kDtF32) emit_chunk<kD32, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
+        else if constexpr (kDt == kDtF16) emit_chunk<kD16, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
+        else if (job.dtype == 0) emit_chunk<kD64, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
+        else if (job.dtype == 1) emit_chunk<kD32, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
+        else emit_chunk<kD16, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
         __syncwarp();
         if (tn >= total_chunks) break;
         t = tn;
@@ -827,15 +867,16 @@ emit_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_
     emit_loop<kWide, kDt>(jobs, njobs, s_single, total_chunks, ctl, smem);
 }
 
-// FP32 form: held to 96 registers (it needs 93 without spilling), so that 20 warps fit an SM
-template <bool kWide>
+// FP32 and FP16 forms: held to 96 registers (FP32 needs 96 without spilling), so that 20 warps
+// fit an SM
+template <bool kWide, int kDt>
 __global__ void __maxnreg__(96)
-emit_kernel_f32(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
+emit_kernel_narrow(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ Job s_single;
     if (threadIdx.x == 0) s_single = single;
     __syncthreads();
-    emit_loop<kWide, kDtF32>(jobs, njobs, s_single, total_chunks, ctl, smem);
+    emit_loop<kWide, kDt>(jobs, njobs, s_single, total_chunks, ctl, smem);
 }
 
 namespace {
@@ -853,10 +894,10 @@ template <bool kWide, int kDt>
 void launch_emit(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
                  cudaStream_t stream) {
     const int w = g_cta_warps[0], smem = w * EmitLayout<kWide>::kBytes;
-    if constexpr (kDt == kDtF32) {
-        const int g = persistent_grid_of(reinterpret_cast<const void *>(emit_kernel_f32<kWide>), w, smem,
+    if constexpr (kDt == kDtF32 || kDt == kDtF16) {
+        const int g = persistent_grid_of(reinterpret_cast<const void *>(emit_kernel_narrow<kWide, kDt>), w, smem,
                                          g_ctas_per_sm[0], total_chunks);
-        emit_kernel_f32<kWide><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+        emit_kernel_narrow<kWide, kDt><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
     } else {
         const int g = persistent_grid_of(reinterpret_cast<const void *>(emit_kernel<kWide, kDt>), w, smem,
                                          g_ctas_per_sm[0], total_chunks);
@@ -908,17 +949,21 @@ cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single, uin
                             Control *ctl, cudaStream_t stream) {
     // the every-row-sparse ablation writes records larger than the plane slots hold
     const bool wide = d_jobs == nullptr && single.variant == kVariantSparse;
-    const int kind = d_jobs != nullptr ? kDtMixed : (single.dtype == 0 ? kDtF64 : kDtF32);
+    const int kind = d_jobs != nullptr ? kDtMixed
+                                       : (single.dtype == 0 ? kDtF64 : (single.dtype == 1 ? kDtF32 : kDtF16));
     if (total_chunks > 0) {
         if (kind == kDtF64) launch_analyse<kDtF64>(d_jobs, njobs, single, total_chunks, ctl, stream);
         else if (kind == kDtF32) launch_analyse<kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
+        else if (kind == kDtF16) launch_analyse<kDtF16>(d_jobs, njobs, single, total_chunks, ctl, stream);
         else launch_analyse<kDtMixed>(d_jobs, njobs, single, total_chunks, ctl, stream);
     }
     {   // the emit launch also writes the header and length of every job, chunks or none
         if (wide && kind == kDtF64) launch_emit<true, kDtF64>(d_jobs, njobs, single, total_chunks, ctl, stream);
-        else if (wide) launch_emit<true, kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
+        else if (wide && kind == kDtF32) launch_emit<true, kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
+        else if (wide) launch_emit<true, kDtF16>(d_jobs, njobs, single, total_chunks, ctl, stream);
         else if (kind == kDtF64) launch_emit<false, kDtF64>(d_jobs, njobs, single, total_chunks, ctl, stream);
         else if (kind == kDtF32) launch_emit<false, kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
+        else if (kind == kDtF16) launch_emit<false, kDtF16>(d_jobs, njobs, single, total_chunks, ctl, stream);
         else launch_emit<false, kDtMixed>(d_jobs, njobs, single, total_chunks, ctl, stream);
     }
     return cudaGetLastError();

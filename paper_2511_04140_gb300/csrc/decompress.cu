@@ -22,13 +22,14 @@ namespace falcon {
 
 namespace {
 
-// Per-warp buffers of a kernel form: one record at a 0..15 byte phase + 16 readable bytes (an
-// FP64 record is at most 19 + 64 * 144 = 9235 bytes, an FP32 one 11 + 32 * 144 = 4619: every
-// row sparse without a zero byte, bitmap + 128 bytes), then W plane slots of 128 bytes and 64
-// u16 sparse-byte totals.  The FP32 form's smaller buffers let more warps stay resident.
-template <bool F64> struct DecLayout {
-    static constexpr int kBuf = F64 ? 9280 : 4672;
-    static constexpr int kPlane = (F64 ? 64 : 32) * 128 + 128;
+// Per-warp buffers of a value kind: one record at a 0..15 byte phase + 16 readable bytes (an
+// FP64 record is at most 19 + 64 * 144 = 9235 bytes, an FP32 one 11 + 32 * 144 = 4619, an FP16
+// one 7 + 16 * 144 = 2311: every row sparse without a zero byte, bitmap + 128 bytes), then W
+// plane slots of 128 bytes and 64 u16 sparse-byte totals.  The narrow kinds' smaller buffers
+// let more warps stay resident.
+template <int D> struct DecLayout {
+    static constexpr int kBuf = D == kD64 ? 9280 : (D == kD32 ? 4672 : 2368);
+    static constexpr int kPlane = Traits<D>::W * 128 + 128;
     static constexpr int kWarpBytes = kBuf + kPlane;
 };
 
@@ -96,7 +97,7 @@ __device__ __forceinline__ void resolve(const Job *jobs, int njobs, const Job &s
 // Largest valid record of a chunk of m values: header, flags, and w = W rows of at most
 // cols/64 + cols/8 bytes (a sparse row with no zero byte).
 __device__ __forceinline__ uint32_t max_record(uint32_t m, uint32_t dtype) {
-    const uint32_t W = dtype == 0 ? 64u : 32u;
+    const uint32_t W = dtype == 0 ? 64u : (dtype == 1 ? 32u : 16u);
     return 3u + W / 8u + W / 8u + W * (chunk_cols(m) / 8u + chunk_cols(m) / 64u);
 }
 
@@ -105,7 +106,7 @@ __device__ __forceinline__ bool issue_record(const Job &job, const Loc &l, uint8
     const uint64_t c = l.t - job.chunk_begin;
     const uint64_t first = c * (uint64_t)job.block;
     const uint32_t m = (uint32_t)((job.n - first) < job.block ? (job.n - first) : job.block);
-    const uint32_t z1b = job.dtype == 0 ? 8u : 4u;
+    const uint32_t z1b = job.dtype == 0 ? 8u : (job.dtype == 1 ? 4u : 2u);
     if (l.size < 3u + z1b || l.size > max_record(m, job.dtype) || l.rec_off + l.size > job.in_bytes) return false;
     const uint8_t *gsrc = job.in + l.rec_off;
     const uint32_t sh = (uint32_t)(reinterpret_cast<uintptr_t>(gsrc) & 15u);
@@ -148,10 +149,10 @@ __device__ __forceinline__ void copy_to_planes(uint8_t *dst, const uint8_t *src,
 
 // `next` starts the copy of the warp's next record into rbuf; it is called exactly once, as
 // soon as this record has been read completely.
-template <bool F64, class Next>
+template <int D, class Next>
 __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const uint8_t *rbuf, uint8_t *pbuf,
                              int lane, Next &&next) {
-    using T = Traits<F64>;
+    using T = Traits<D>;
     using U = typename T::U;
 
     const uint64_t c = l.t - job.chunk_begin;
@@ -264,7 +265,7 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
         return *reinterpret_cast<const uint32_t *>(planes + (63 - p) * 128 + 4 * lane);
     };
     U d[32];
-    if constexpr (F64) {
+    if constexpr (D == 0) {
         if (w > 32) {
             uint32_t a[32];
 #pragma unroll
@@ -281,10 +282,10 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     {
         uint32_t a[32];
 #pragma unroll
-        for (int p = 0; p < 32; ++p) a[p] = plane_word(p);
+        for (int p = 0; p < 32; ++p) a[p] = p < T::W ? plane_word(p) : 0u;    // FP16: 16 planes
         transpose32(a);
         const uint32_t keep = w >= 32 ? ~0u : ((1u << w) - 1u);
-        if constexpr (F64) {
+        if constexpr (D == 0) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) d[k] |= (U)(a[k ^ 7] & keep);
         } else {
@@ -296,12 +297,12 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
 #pragma unroll
     for (int k = 0; k < 32; ++k) { run += unzigzag(d[k]); d[k] = run; }
     U lane_off;
-    if constexpr (F64) lane_off = warp_exclusive_u64(run, lane);
+    if constexpr (D == 0) lane_off = warp_exclusive_u64(run, lane);
     else lane_off = (U)warp_exclusive_u64((uint64_t)run, lane);
     const U gbase = z1 + lane_off;               // G of value 32*lane + k + 1 = gbase + d[k]
     const bool case1 = alpha <= (uint32_t)T::A_MAX && beta_hat <= (uint32_t)T::B_MAX;
     if (case1) {
-        if constexpr (F64) {
+        if constexpr (D == 0) {
             // |g| >= 2^53 only in streams no encoder writes: then every value takes the FP64 path
             bool big = false;
 #pragma unroll
@@ -317,9 +318,12 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
 #pragma unroll
                 for (int k = 0; k < 32; ++k) d[k] = div_pow10_exact((int64_t)(gbase + d[k]), (int)alpha);
             }
-        } else {
+        } else if constexpr (D == kD32) {
 #pragma unroll
             for (int k = 0; k < 32; ++k) d[k] = (U)__float_as_uint(div_pow10((int32_t)(gbase + d[k]), (int)alpha));
+        } else {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) d[k] = div_pow10_h((int16_t)(U)(gbase + d[k]), (int)alpha);
         }
     } else {
 #pragma unroll
@@ -327,12 +331,14 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     }
     U v0;
     if (case1) {
-        if constexpr (F64) {
+        if constexpr (D == 0) {
             const uint64_t g1 = z1;
             v0 = ((g1 + (1ull << 53)) > (1ull << 54)) ? (U)__double_as_longlong(div_pow10((int64_t)g1, (int)alpha))
                                                        : div_pow10_exact((int64_t)g1, (int)alpha);
-        } else {
+        } else if constexpr (D == kD32) {
             v0 = (U)__float_as_uint(div_pow10((int32_t)z1, (int)alpha));
+        } else {
+            v0 = div_pow10_h((int16_t)z1, (int)alpha);
         }
     } else {
         v0 = unzigzag(z1);
@@ -351,15 +357,18 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
 #pragma unroll
     for (int u = 0; u < UN; ++u) {
         uint4 q;
-        if constexpr (F64) {
+        if constexpr (D == 0) {
             q = make_uint4((uint32_t)d[2 * u], (uint32_t)((uint64_t)d[2 * u] >> 32),
                            (uint32_t)d[2 * u + 1], (uint32_t)((uint64_t)d[2 * u + 1] >> 32));
-        } else {
+        } else if constexpr (D == kD32) {
             q = make_uint4((uint32_t)d[4 * u], (uint32_t)d[4 * u + 1], (uint32_t)d[4 * u + 2], (uint32_t)d[4 * u + 3]);
+        } else {
+            q = make_uint4((uint32_t)d[8 * u] | ((uint32_t)d[8 * u + 1] << 16), (uint32_t)d[8 * u + 2] | ((uint32_t)d[8 * u + 3] << 16),
+                           (uint32_t)d[8 * u + 4] | ((uint32_t)d[8 * u + 5] << 16), (uint32_t)d[8 * u + 6] | ((uint32_t)d[8 * u + 7] << 16));
         }
-        *reinterpret_cast<uint4 *>(pbuf + (lane * UN + (u ^ (lane & 7))) * 16) = q;
+        *reinterpret_cast<uint4 *>(pbuf + (lane * UN + unit_swizzle<D>(lane, u)) * 16) = q;
     }
-    if (m > 1024u && lane == 31) *reinterpret_cast<U *>(pbuf + phys_elem_byte<F64>(1024)) = vx;
+    if (m > 1024u && lane == 31) *reinterpret_cast<U *>(pbuf + phys_elem_byte<D>(1024)) = vx;
     __syncwarp();
     uint8_t *dst = job.out + first * T::S;
     const uint32_t nbytes = m * T::S;
@@ -367,11 +376,11 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
         const uint32_t nunits = nbytes >> 4;
         for (uint32_t q = lane; q < nunits; q += 32)
-            *reinterpret_cast<uint4 *>(dst + 16u * q) = *reinterpret_cast<const uint4 *>(pbuf + phys_unit<F64>(q) * 16u);
+            *reinterpret_cast<uint4 *>(dst + 16u * q) = *reinterpret_cast<const uint4 *>(pbuf + phys_unit<D>(q) * 16u);
         done = (nunits * 16u) / T::S;
     }
     for (uint32_t e = done + lane; e < m; e += 32)
-        *reinterpret_cast<U *>(dst + (size_t)e * T::S) = *reinterpret_cast<const U *>(pbuf + phys_elem_byte<F64>(e));
+        *reinterpret_cast<U *>(dst + (size_t)e * T::S) = *reinterpret_cast<const U *>(pbuf + phys_elem_byte<D>(e));
     __syncwarp();
 }
 
@@ -387,7 +396,9 @@ offsets_kernel(const Job *__restrict__ jobs, Job single) {
 }
 
 // Forms by dtype: kDt = 0 (every job FP64), 1 (every job FP32), 2 (either, per job).
-constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2;
+constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2, kDtF16 = 3;
+// the value kind whose buffers a form needs (the either-dtype form: the largest)
+template <int kDt> constexpr int layout_kind() { return kDt == kDtF32 ? kD32 : (kDt == kDtF16 ? kD16 : kD64); }
 
 template <int kDt>
 __global__ void __launch_bounds__(32 * kMaxDecompressWarps, 1)
@@ -395,7 +406,7 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    using L = DecLayout<kDt != kDtF32>;
+    using L = DecLayout<layout_kind<kDt>()>;
     uint8_t *wbase = smem + warp * L::kWarpBytes;
     uint8_t *pbuf = wbase + L::kBuf;
     __shared__ Job s_single;                      // the single job, read from shared memory
@@ -436,10 +447,12 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
             cp_async_commit();
         };
         const Job &job = job_of(jobs, njobs, s_single, t);
-        if constexpr (kDt == kDtF64) decode_chunk<true>(job, lc, okc, wbase, pbuf, lane, next);
-        else if constexpr (kDt == kDtF32) decode_chunk<false>(job, lc, okc, wbase, pbuf, lane, next);
-        else if (job.dtype == 0) decode_chunk<true>(job, lc, okc, wbase, pbuf, lane, next);
-        else decode_chunk<false>(job, lc, okc, wbase, pbuf, lane, next);
+        if constexpr (kDt == kDtF64) decode_chunk<kD64>(job, lc, okc, wbase, pbuf, lane, next);
+        else if constexpr (kDt == kDtF32) decode_chunk<kD32>(job, lc, okc, wbase, pbuf, lane, next);
+        else if constexpr (kDt == kDtF16) decode_chunk<kD16>(job, lc, okc, wbase, pbuf, lane, next);
+        else if (job.dtype == 0) decode_chunk<kD64>(job, lc, okc, wbase, pbuf, lane, next);
+        else if (job.dtype == 1) decode_chunk<kD32>(job, lc, okc, wbase, pbuf, lane, next);
+        else decode_chunk<kD16>(job, lc, okc, wbase, pbuf, lane, next);
         if (tn >= total_chunks) break;
         t = tn;
         tn = tnn;
@@ -453,7 +466,7 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
 int decompress_grid(uint64_t total_chunks) {
     const int w = g_cta_warps[1];
     return persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDtMixed>), w,
-                                w * DecLayout<true>::kWarpBytes,
+                                w * DecLayout<kD64>::kWarpBytes,
                                 g_ctas_per_sm[1], total_chunks);
 }
 
@@ -461,7 +474,7 @@ namespace {
 template <int kDt>
 void launch_decode(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
                    cudaStream_t stream) {
-    const int w = g_cta_warps[1], smem = w * DecLayout<kDt != kDtF32>::kWarpBytes;
+    const int w = g_cta_warps[1], smem = w * DecLayout<layout_kind<kDt>()>::kWarpBytes;
     const int grid = persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDt>), w, smem,
                                           g_ctas_per_sm[1], total_chunks);
     decompress_kernel<kDt><<<grid, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
@@ -473,7 +486,8 @@ cudaError_t launch_decompress(const Job *d_jobs, int njobs, const Job &single, u
     offsets_kernel<<<(d_jobs != nullptr) ? njobs : 1, 1024, 0, stream>>>(d_jobs, single);
     if (d_jobs != nullptr) launch_decode<kDtMixed>(d_jobs, njobs, single, total_chunks, ctl, stream);
     else if (single.dtype == 0) launch_decode<kDtF64>(d_jobs, njobs, single, total_chunks, ctl, stream);
-    else launch_decode<kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
+    else if (single.dtype == 1) launch_decode<kDtF32>(d_jobs, njobs, single, total_chunks, ctl, stream);
+    else launch_decode<kDtF16>(d_jobs, njobs, single, total_chunks, ctl, stream);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 // little-endian bytes are row bytes 4l .. 4l+3 of that plane (Sec. 3.3, Fig. 8).
 #pragma once
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "falcon_internal.h"
@@ -17,8 +18,11 @@ namespace falcon {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-template <bool F64> struct Traits;
-template <> struct Traits<true> {
+// Value kinds of the kernels: D = 0 FP64, 1 FP32, 2 FP16 (binary16, R18).  U holds a value's
+// bit pattern and every integer derived from it (G, Z) modulo 2^W.
+constexpr int kD64 = 0, kD32 = 1, kD16 = 2;
+template <int D> struct Traits;
+template <> struct Traits<kD64> {
     using U = uint64_t;
     static constexpr int W = 64;            // bits per value
     static constexpr int S = 8;             // bytes per value
@@ -29,7 +33,7 @@ template <> struct Traits<true> {
     static constexpr int B_SENT = 16;
     static constexpr int UNITS = 16;        // 16-byte units per lane (32 values)
 };
-template <> struct Traits<false> {
+template <> struct Traits<kD32> {
     using U = uint32_t;
     static constexpr int W = 32;
     static constexpr int S = 4;
@@ -39,6 +43,17 @@ template <> struct Traits<false> {
     static constexpr int A_SENT = 11;
     static constexpr int B_SENT = 8;
     static constexpr int UNITS = 8;
+};
+template <> struct Traits<kD16> {
+    using U = uint16_t;
+    static constexpr int W = 16;
+    static constexpr int S = 2;
+    static constexpr int Z1B = 2;
+    static constexpr int A_MAX = 4;         // 5^4 < 2^11: 10^alpha exact in binary16
+    static constexpr int B_MAX = 3;         // 10^3 < 2^11
+    static constexpr int A_SENT = 5;
+    static constexpr int B_SENT = 4;
+    static constexpr int UNITS = 4;
 };
 
 // --------------------------------------------------------------------------------------
@@ -80,6 +95,10 @@ __device__ __forceinline__ uint64_t zigzag(uint64_t x) { return (x << 1) ^ (uint
 __device__ __forceinline__ uint32_t zigzag(uint32_t x) { return (x << 1) ^ (uint32_t)((int32_t)x >> 31); }
 __device__ __forceinline__ uint64_t unzigzag(uint64_t z) { return (z >> 1) ^ (0ull - (z & 1ull)); }
 __device__ __forceinline__ uint32_t unzigzag(uint32_t z) { return (z >> 1) ^ (0u - (z & 1u)); }
+__device__ __forceinline__ uint16_t zigzag(uint16_t x) {
+    return (uint16_t)(((uint32_t)x << 1) ^ (uint32_t)((int32_t)(int16_t)x >> 15));
+}
+__device__ __forceinline__ uint16_t unzigzag(uint16_t z) { return (uint16_t)((z >> 1) ^ (0u - (z & 1u))); }
 
 __device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
     return ((uint64_t)__shfl_sync(kFull, (uint32_t)(v >> 32), src) << 32) |
@@ -99,6 +118,11 @@ __device__ __forceinline__ uint32_t shfl_down_x(uint32_t v, int d) { return __sh
 __device__ __forceinline__ uint64_t shfl_down_x(uint64_t v, int d) { return shfl_down_u64(v, d); }
 __device__ __forceinline__ uint32_t shfl_up_x(uint32_t v, int d) { return __shfl_up_sync(kFull, v, d); }
 __device__ __forceinline__ uint64_t shfl_up_x(uint64_t v, int d) { return shfl_up_u64(v, d); }
+__device__ __forceinline__ uint16_t shfl_x(uint16_t v, int src) { return (uint16_t)__shfl_sync(kFull, (uint32_t)v, src); }
+__device__ __forceinline__ uint16_t shfl_down_x(uint16_t v, int d) {
+    return (uint16_t)__shfl_down_sync(kFull, (uint32_t)v, d);
+}
+__device__ __forceinline__ uint16_t shfl_up_x(uint16_t v, int d) { return (uint16_t)__shfl_up_sync(kFull, (uint32_t)v, d); }
 
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 #pragma unroll
@@ -114,6 +138,8 @@ __device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
 __device__ __forceinline__ uint32_t warp_max_x(uint32_t v) { return __reduce_max_sync(kFull, v); }
 __device__ __forceinline__ uint64_t warp_max_x(uint64_t v) { return warp_max_u64(v); }
 __device__ __forceinline__ uint32_t warp_or_x(uint32_t v) { return __reduce_or_sync(kFull, v); }
+__device__ __forceinline__ uint16_t warp_max_x(uint16_t v) { return (uint16_t)__reduce_max_sync(kFull, (uint32_t)v); }
+__device__ __forceinline__ uint16_t warp_or_x(uint16_t v) { return (uint16_t)__reduce_or_sync(kFull, (uint32_t)v); }
 __device__ __forceinline__ uint64_t warp_or_x(uint64_t v) {
     return ((uint64_t)__reduce_or_sync(kFull, (uint32_t)(v >> 32)) << 32) | __reduce_or_sync(kFull, (uint32_t)v);
 }
@@ -179,24 +205,31 @@ __device__ __forceinline__ void transpose32(uint32_t (&a)[32]) {
 // Shared-memory staging of a chunk's values, swizzled so that lane l's 16-byte units
 // (values 32l .. 32l+31) are read conflict-free: unit u of lane L sits at L*UNITS + (u^(L&7)).
 // --------------------------------------------------------------------------------------
-template <bool F64>
-__device__ __forceinline__ uint32_t phys_unit(uint32_t q) {
-    constexpr int UN = Traits<F64>::UNITS;
-    uint32_t L = q / UN, u = q % UN;
-    return L * UN + (u ^ (L & 7u));
+template <int D>
+__device__ __forceinline__ uint32_t unit_swizzle(uint32_t L, uint32_t u) {
+    // lane L's unit u: every 8 consecutive lanes reading their unit u hit 8 distinct 16-byte
+    // bank groups (FP16 has 4 units per lane, so lanes L and L + 4 differ by the XOR)
+    constexpr int UN = Traits<D>::UNITS;
+    return u ^ (UN >= 8 ? (L & 7u) : ((L >> 1) & 3u));
 }
-template <bool F64>
+template <int D>
+__device__ __forceinline__ uint32_t phys_unit(uint32_t q) {
+    constexpr int UN = Traits<D>::UNITS;
+    uint32_t L = q / UN, u = q % UN;
+    return L * UN + unit_swizzle<D>(L, u);
+}
+template <int D>
 __device__ __forceinline__ uint32_t phys_elem_byte(uint32_t e) {
-    constexpr int S = Traits<F64>::S;
+    constexpr int S = Traits<D>::S;
     constexpr int PER = 16 / S;       // values per unit
-    return phys_unit<F64>(e / PER) * 16u + (e % PER) * S;
+    return phys_unit<D>(e / PER) * 16u + (e % PER) * S;
 }
 
 // Starts loading m values (m <= 1025) from global src into a warp staging buffer
 // (cp.async; the caller commits and waits).
-template <bool F64>
+template <int D>
 __device__ __forceinline__ void stage_values_async(const uint8_t *src, uint32_t m, uint8_t *wsm, int lane) {
-    constexpr int S = Traits<F64>::S;
+    constexpr int S = Traits<D>::S;
     const uint32_t base = smem_addr(wsm);
     const uint32_t nbytes = m * S;
     uint32_t done = 0;
@@ -208,33 +241,42 @@ __device__ __forceinline__ void stage_values_async(const uint8_t *src, uint32_t 
 #pragma unroll
             for (uint32_t i = 0; i < FULL_UNITS / 32u; ++i) {
                 const uint32_t q = lane + 32u * i;
-                cp_async16(base + phys_unit<F64>(q) * 16u, src + 16u * q);
+                cp_async16(base + phys_unit<D>(q) * 16u, src + 16u * q);
             }
-            for (uint32_t q = FULL_UNITS + lane; q < nunits; q += 32) cp_async16(base + phys_unit<F64>(q) * 16u, src + 16u * q);
+            for (uint32_t q = FULL_UNITS + lane; q < nunits; q += 32) cp_async16(base + phys_unit<D>(q) * 16u, src + 16u * q);
         } else {
-            for (uint32_t q = lane; q < nunits; q += 32) cp_async16(base + phys_unit<F64>(q) * 16u, src + 16u * q);
+            for (uint32_t q = lane; q < nunits; q += 32) cp_async16(base + phys_unit<D>(q) * 16u, src + 16u * q);
         }
         done = (nunits * 16u) / S;
     }
     for (uint32_t e = done + lane; e < m; e += 32) {
-        if constexpr (F64) cp_async8(base + phys_elem_byte<F64>(e), src + (size_t)e * S);
-        else cp_async4(base + phys_elem_byte<F64>(e), src + (size_t)e * S);
+        if constexpr (D == kD64) cp_async8(base + phys_elem_byte<D>(e), src + (size_t)e * S);
+        else if constexpr (D == kD32) cp_async4(base + phys_elem_byte<D>(e), src + (size_t)e * S);
+        else                                     // no 2-byte cp.async: a plain copy (visible at the next __syncwarp)
+            *reinterpret_cast<uint16_t *>(wsm + phys_elem_byte<D>(e)) = *reinterpret_cast<const uint16_t *>(src + (size_t)e * S);
     }
 }
 
 // Lane reads its 32 values (indices 32*lane + k); indices >= m read as +0.
-template <bool F64>
+template <int D>
 __device__ __forceinline__ void read_own(const uint8_t *wsm, int lane, uint32_t m,
-                                         typename Traits<F64>::U (&v)[32]) {
-    using U = typename Traits<F64>::U;
-    constexpr int UN = Traits<F64>::UNITS;
+                                         typename Traits<D>::U (&v)[32]) {
+    using U = typename Traits<D>::U;
+    constexpr int UN = Traits<D>::UNITS;
     constexpr int PER = 32 / UN;
 #pragma unroll
     for (int u = 0; u < UN; ++u) {
-        const uint4 q = *reinterpret_cast<const uint4 *>(wsm + (lane * UN + (u ^ (lane & 7))) * 16);
-        if constexpr (F64) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(wsm + (lane * UN + unit_swizzle<D>(lane, u)) * 16);
+        if constexpr (D == kD64) {
             v[PER * u + 0] = ((U)q.y << 32) | q.x;
             v[PER * u + 1] = ((U)q.w << 32) | q.z;
+        } else if constexpr (D == kD16) {
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                v[PER * u + 2 * h] = (U)(w4[h] & 0xFFFFu);
+                v[PER * u + 2 * h + 1] = (U)(w4[h] >> 16);
+            }
         } else {
             v[PER * u + 0] = q.x;
             v[PER * u + 1] = q.y;
@@ -249,10 +291,10 @@ __device__ __forceinline__ void read_own(const uint8_t *wsm, int lane, uint32_t 
     }
 }
 
-template <bool F64>
-__device__ __forceinline__ typename Traits<F64>::U read_elem(const uint8_t *wsm, uint32_t e) {
-    using U = typename Traits<F64>::U;
-    return *reinterpret_cast<const U *>(wsm + phys_elem_byte<F64>(e));
+template <int D>
+__device__ __forceinline__ typename Traits<D>::U read_elem(const uint8_t *wsm, uint32_t e) {
+    using U = typename Traits<D>::U;
+    return *reinterpret_cast<const U *>(wsm + phys_elem_byte<D>(e));
 }
 
 // --------------------------------------------------------------------------------------
@@ -265,6 +307,10 @@ __device__ __forceinline__ bool is_special(uint64_t u) {
 __device__ __forceinline__ bool is_special(uint32_t u) {
     const uint32_t a = u & 0x7FFFFFFFu;
     return (u != 0) && (a - 0x00800000u >= 0x7F000000u);
+}
+__device__ __forceinline__ bool is_special(uint16_t u) {
+    const uint32_t a = u & 0x7FFFu;
+    return (u != 0) && (a - 0x0400u >= 0x7800u);
 }
 
 // floor(log10 a) as the largest k with a >= fl(10^k), for a normal, positive, with binary
@@ -283,6 +329,13 @@ __device__ __forceinline__ int floor_log10(uint32_t a) {
     else if (a < FALCON_P10_F32[k - FALCON_P10_F32_LO]) --k;
     return k;
 }
+__device__ __forceinline__ int floor_log10(uint16_t a) {
+    const int e2 = (int)(a >> 10) - 15;
+    int k = (e2 * 78913) >> 18;
+    if (k < FALCON_P10_F16_HI && a >= FALCON_P10_F16[k + 1 - FALCON_P10_F16_LO]) ++k;
+    else if (a < FALCON_P10_F16[k - FALCON_P10_F16_LO]) --k;
+    return k;
+}
 // binary-exponent window where floor_log10 is defined and Case 1 is reachable
 __device__ __forceinline__ bool log10_in_range(uint64_t a) {
     const uint32_t be = (uint32_t)(a >> 52);
@@ -292,6 +345,7 @@ __device__ __forceinline__ bool log10_in_range(uint32_t a) {
     const uint32_t be = a >> 23;
     return be >= 127u - 40u && be < 127u + 24u;
 }
+__device__ __forceinline__ bool log10_in_range(uint16_t) { return true; }   // every normal binary16
 
 // --------------------------------------------------------------------------------------
 // The per-value test of Alg. 2 at decimal place a, in exact integer arithmetic.
@@ -416,6 +470,76 @@ __device__ __forceinline__ uint32_t case1_g(uint32_t u, int a) {
     if (F <= 0) N = P << (-F);
     else N = (P + (1ull << (F - 1))) >> F;
     return (u >> 31) ? (0u - (uint32_t)N) : (uint32_t)N;
+}
+
+// binary16 (R18): both tests of Alg. 2 at decimal place a from one product, as for FP32:
+// v = m 2^E with an 11-bit m, P = m 5^a < 2^21, F = -(E + a) <= 24; eps <= mu is
+// dist(P, 2^F Z) <= P 2^-10 and the round trip |N 2^F - P| < 5^a / 2 (5^a / 4 below a power
+// of two, where the ulp below v is half as wide).
+__device__ __forceinline__ bool alg2_step_f16(uint16_t u, int a, bool &rt) {
+    const uint32_t au = u & 0x7FFFu;
+    const int F = 25 - (int)(au >> 10) - a;
+    if (au == 0 || F <= 0) { rt = true; return true; }
+    const uint32_t m = (au & 0x3FFu) | 0x400u;
+    const uint32_t p5 = (uint32_t)FALCON_POW5[a];            // 5^a <= 625
+    const uint32_t P = m * p5;
+    const uint32_t lim = p5 >> 1, lim_low = (m == 0x400u) ? ((p5 - 1u) >> 2) : lim;
+    const uint32_t mask = (1u << F) - 1u;
+    const uint32_t r = P & mask, rc = mask - r + 1u;
+    rt = (r > (mask >> 1)) ? (rc <= lim) : (r <= lim_low);
+    return (r < rc ? r : rc) <= (P >> 10);
+}
+__device__ __forceinline__ bool q_test(uint16_t u, int a) {
+    bool rt;
+    (void)alg2_step_f16(u, a, rt);
+    return rt;
+}
+// Alg. 2's decimal place of one binary16 value within [0, atop]: the first a with eps <= mu,
+// -1 if the round trip fails there (an early stop) or no a passes
+__device__ __forceinline__ int first_pass_f16(uint16_t u, int atop) {
+    if ((u & 0x7FFFu) == 0) return 0;
+    for (int a = 0; a <= atop; ++a) {
+        bool rt;
+        if (alg2_step_f16(u, a, rt)) return rt ? a : -1;
+    }
+    return -1;
+}
+__device__ __forceinline__ uint16_t case1_g(uint16_t u, int a) {
+    const uint32_t au = u & 0x7FFFu;
+    if (au == 0) return 0;
+    const int F = 25 - (int)(au >> 10) - a;
+    const uint32_t P = ((au & 0x3FFu) | 0x400u) * (uint32_t)FALCON_POW5[a];
+    const uint32_t N = F <= 0 ? (P << (-F)) : ((P + (1u << (F - 1))) >> F);
+    return (uint16_t)((u >> 15) ? (0u - N) : N);
+}
+
+// fl16(g / 10^a) (R18), correctly rounded, for |g| <= 2^15 and 0 <= a <= 4: the quotient by 5^a
+// as in div_pow10_exact below, rounded at 11 significant bits instead of 53 (the result is
+// normal: |g| / 10^a >= 10^-4).  Returns the binary16 pattern.
+__device__ __forceinline__ uint16_t div_pow10_h(int32_t g, int a) {
+    if (g == 0) return 0;
+    const uint32_t sign = g < 0 ? 0x8000u : 0u;
+    const uint64_t ag = g < 0 ? (uint64_t)(-(int64_t)g) : (uint64_t)g;
+    const int s = __clzll((long long)ag);
+    const uint64_t G = ag << s;
+    uint64_t T = G, r = 0;
+    int d = 0;
+    if (a > 0) {
+        d = FALCON_LOG2_POW5[a];
+        const uint64_t D = FALCON_POW5[a];
+        T = __umul64hi(G, FALCON_RECIP5[a]);
+        r = (G << d) - T * D;
+        if (r >= D) { r -= D; ++T; }
+    }
+    const int lz = __clzll((long long)T);
+    const uint64_t Tn = T << lz;
+    uint32_t mant = (uint32_t)(Tn >> 53);
+    const uint64_t rest = Tn & ((1ull << 53) - 1ull);
+    const bool sticky = (rest & ((1ull << 52) - 1ull)) != 0ull || r != 0;
+    if ((rest >> 52) && (sticky || (mant & 1u))) ++mant;
+    int e2 = 53 - lz - d - s - a;               // the value is mant * 2^e2
+    if (mant == 2048u) { mant = 1024u; ++e2; }
+    return (uint16_t)(sign | ((uint32_t)(e2 + 25) << 10) | (mant & 0x3FFu));
 }
 
 // fl(g / 10^a), correctly rounded (nearest, ties to even), for |g| < 2^53 and 0 <= a <= 22, in

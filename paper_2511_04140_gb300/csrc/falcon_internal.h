@@ -58,6 +58,10 @@ constexpr size_t kControlBytes = 256;   // control block region (keeps flags 256
 // dense-row mask), then one per 64-chunk tile and one per 4096-chunk group (the sums of their
 // record sizes, which the analysis adds up); decompression keeps the record offset of each tile
 // in the first words.
+// value kinds of the stream format: 0 FP64, 1 FP32, 2 FP16 (binary16)
+inline bool dtype_valid(int dtype) { return dtype >= 0 && dtype <= 2; }
+inline size_t dtype_bytes(int dtype) { return dtype == 0 ? 8 : (dtype == 1 ? 4 : 2); }
+
 constexpr uint64_t kTile = 64;
 constexpr uint64_t kGroup = 4096;
 __host__ __device__ constexpr uint64_t tile_count(uint64_t nchunks) { return (nchunks + kTile - 1) / kTile; }

@@ -10,6 +10,8 @@
 #define FALCON_P10_F64_HI (22)
 #define FALCON_P10_F32_LO (-15)
 #define FALCON_P10_F32_HI (10)
+#define FALCON_P10_F16_LO (-8)
+#define FALCON_P10_F16_HI (4)
 
 FALCON_TABLE_QUAL uint64_t FALCON_POW5[23] = {
     0x0000000000000001ull, /* 5^0 */
@@ -176,5 +178,21 @@ FALCON_TABLE_QUAL uint32_t FALCON_P10_F32[26] = {
     0x4cbebc20u, /* fl32(1e8) */
     0x4e6e6b28u, /* fl32(1e9) */
     0x501502f9u, /* fl32(1e10) */
+};
+
+FALCON_TABLE_QUAL uint16_t FALCON_P10_F16[13] = {
+    0x0000u, /* fl16(1e-8) */
+    0x0002u, /* fl16(1e-7) */
+    0x0011u, /* fl16(1e-6) */
+    0x00a8u, /* fl16(1e-5) */
+    0x068eu, /* fl16(1e-4) */
+    0x1419u, /* fl16(1e-3) */
+    0x211fu, /* fl16(1e-2) */
+    0x2e66u, /* fl16(1e-1) */
+    0x3c00u, /* fl16(1e0) */
+    0x4900u, /* fl16(1e1) */
+    0x5640u, /* fl16(1e2) */
+    0x63d0u, /* fl16(1e3) */
+    0x70e2u, /* fl16(1e4) */
 };
 

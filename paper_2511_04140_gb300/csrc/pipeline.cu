@@ -151,12 +151,12 @@ int falcon_pipeline_compress(const void *h_in, uint64_t n, int dtype, uint32_t b
 int falcon_pipeline_compress_with(const void *h_in, uint64_t n, int dtype, uint32_t block_size,
                                   uint64_t frame_values, int nstreams, int scheduler, void *h_out,
                                   size_t out_capacity, uint64_t *h_frame_bytes, size_t *out_bytes) {
-    if ((dtype != FALCON_F64 && dtype != FALCON_F32) || !h_out || !out_bytes || !h_frame_bytes) return FALCON_ERR_INVALID;
+    if (!falcon::dtype_valid(dtype) || !h_out || !out_bytes || !h_frame_bytes) return FALCON_ERR_INVALID;
     if (n > 0 && !h_in) return FALCON_ERR_INVALID;
     if (frame_values == 0 || nstreams < 1 || nstreams > 256) return FALCON_ERR_INVALID;
     if (scheduler < FALCON_SCHED_EVENT_DRIVEN || scheduler > FALCON_SCHED_PRE_ALLOCATION) return FALCON_ERR_INVALID;
     if (falcon_bound(frame_values, dtype, block_size) == 0) return FALCON_ERR_INVALID;
-    const size_t s = dtype == FALCON_F64 ? 8 : 4;
+    const size_t s = falcon::dtype_bytes(dtype);
     const uint64_t nframes = (n + frame_values - 1) / frame_values;
     const uint64_t fchunks = (frame_values + block_size - 1) / block_size;
     const size_t fbound = falcon_bound(frame_values, dtype, block_size);
@@ -303,7 +303,7 @@ int falcon_pipeline_decompress(const void *h_in, const uint64_t *h_frame_bytes, 
         uint32_t blk = 0;
         const int st = falcon_stream_info(in8 + ioff, h_frame_bytes[f], &nv, &dt, &blk, &nc);
         if (st) return st;
-        const size_t s = dt == FALCON_F64 ? 8 : 4;
+        const size_t s = falcon::dtype_bytes(dt);
         in_off[f] = ioff;
         out_off[f] = ooff;
         nvals[f] = nv;
@@ -335,7 +335,7 @@ int falcon_pipeline_decompress(const void *h_in, const uint64_t *h_frame_bytes, 
                     st = falcon_decompress_async(sl.d_in, h_frame_bytes[f], in8 + in_off[f], sl.d_out, max_vals, sl.d_ws,
                                                  falcon_workspace_bytes(max_chunks), sl.d_res, sl.stream);
                     if (st) return st;
-                    const size_t s = (in8[in_off[f] + 5] == FALCON_F64) ? 8 : 4;
+                    const size_t s = falcon::dtype_bytes(in8[in_off[f] + 5]);
                     if (cudaMemcpyAsync(out8 + out_off[f], sl.d_out, nvals[f] * s, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
                         return FALCON_ERR_CUDA;
                     if (cudaMemcpyAsync(sl.h_res, sl.d_res, 16, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)

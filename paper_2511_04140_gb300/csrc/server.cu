@@ -127,7 +127,7 @@ struct Batch {
     std::vector<Request> reqs;
 };
 
-size_t elem(int dtype) { return dtype == FALCON_F64 ? 8 : 4; }
+size_t elem(int dtype) { return dtype_bytes(dtype); }
 
 }  // namespace
 
@@ -523,7 +523,7 @@ int falcon_server_submit(falcon_server *s, int op, const void *h_in, uint64_t co
     r.op = op;
     r.h_in = static_cast<const uint8_t *>(h_in);
     if (op == FALCON_COMPRESS) {
-        if (dtype != FALCON_F64 && dtype != FALCON_F32) return FALCON_ERR_INVALID;
+        if (!dtype_valid(dtype)) return FALCON_ERR_INVALID;
         if (block_size < 2 || block_size > kMaxBlock) return FALCON_ERR_INVALID;
         if (count > 0 && !h_in) return FALCON_ERR_INVALID;
         if (count > (1ull << 58)) return FALCON_ERR_CAPACITY;

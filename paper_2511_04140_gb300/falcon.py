@@ -15,7 +15,7 @@ import torch
 
 from . import build as _build
 
-F64, F32 = 0, 1
+F64, F32, F16 = 0, 1, 2
 OK, ERR_INVALID, ERR_CAPACITY, ERR_CORRUPT, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 HEADER_BYTES = 32
 MAX_BLOCK = 1025
@@ -134,7 +134,14 @@ def _dtype_code(t: torch.Tensor) -> int:
         return F64
     if t.dtype == torch.float32:
         return F32
+    if t.dtype == torch.float16:
+        return F16
     raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def torch_dtype(code: int) -> torch.dtype:
+    """The torch dtype of a stream's dtype code (FALCON_F64 / F32 / F16)."""
+    return {F64: torch.float64, F32: torch.float32, F16: torch.float16}[code]
 
 
 def _stream_ptr(stream) -> int:
@@ -193,7 +200,7 @@ def decompress(s: torch.Tensor, out: torch.Tensor | None = None, stream=None) ->
     if len(hdr) < HEADER_BYTES:
         raise FalconError(ERR_CORRUPT, "decompress")
     n, code, _, _ = stream_info(hdr)
-    dtype = torch.float64 if code == F64 else torch.float32
+    dtype = torch_dtype(code)
     if out is None:
         out = torch.empty(max(n, 1), dtype=dtype, device=s.device)
     n_out = ctypes.c_uint64()
@@ -298,7 +305,7 @@ class Batch:
                 hb = ctypes.create_string_buffer(bytes(hdr)[:HEADER_BYTES], HEADER_BYTES)
                 self._headers.append(hb)
                 nval, code, _, _ = stream_info(bytes(hdr))
-                dtype = torch.float64 if code == F64 else torch.float32
+                dtype = torch_dtype(code)
                 out = outputs[i] if outputs is not None else torch.empty(max(nval, 1), dtype=dtype, device=s_t.device)
                 sr.d_in, sr.d_out, sr.in_bytes = s_t.data_ptr(), out.data_ptr(), nbytes
                 sr.out_capacity = out.numel() * out.element_size()
@@ -373,7 +380,7 @@ def pipeline_decompress(s: torch.Tensor, frame_bytes, nstreams: int = 16, out: t
                 nv, code, _, _ = stream_info(s[off:off + HEADER_BYTES].numpy().tobytes())
                 tot += nv
                 off += b
-            n, dtype = tot, (torch.float64 if code == F64 else torch.float32)
+            n, dtype = tot, torch_dtype(code)
         out = torch.empty(max(n, 1), dtype=dtype, pin_memory=torch.cuda.is_available())
     n_out = ctypes.c_uint64()
     _check(_load().falcon_pipeline_decompress(s.data_ptr(), fb, nframes, nstreams, out.data_ptr(),

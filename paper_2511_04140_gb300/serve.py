@@ -127,8 +127,7 @@ class Server:
         if c.op == falcon.COMPRESS:
             dtype = torch.uint8
         else:
-            es = nbytes // c.values if c.values else (8 if int(payload[5]) == falcon.F64 else 4)
-            dtype = torch.float64 if es == 8 else torch.float32
+            dtype = falcon.torch_dtype(int(payload[5]))
         raw = (ctypes.c_uint8 * nbytes).from_address(c.h_out) if nbytes else bytearray(0)
         arr = np.frombuffer(raw, dtype=np.uint8)
         weakref.finalize(arr, self._free, c.h_out)        # arena space back when unreferenced
@@ -235,7 +234,7 @@ def run_one_at_a_time(pool, rate: float, duration: float, seed: int = 0, device=
             out_max = max(out_max, falcon.bound(p.numel(), falcon._dtype_code(p), block))
         else:
             n, code, _, _ = falcon.stream_info(p[:falcon.HEADER_BYTES].numpy().tobytes())
-            out_max = max(out_max, n * (8 if code == falcon.F64 else 4))
+            out_max = max(out_max, n * torch.empty(0, dtype=falcon.torch_dtype(code)).element_size())
     d_in = torch.empty((in_max + 15) // 16 * 16, dtype=torch.uint8, device=dev)
     d_out = torch.empty(max(out_max, 32) // 8 * 8 + 8, dtype=torch.uint8, device=dev)
     h_out = torch.empty(max(out_max, 32), dtype=torch.uint8, pin_memory=True)
@@ -255,8 +254,7 @@ def run_one_at_a_time(pool, rate: float, duration: float, seed: int = 0, device=
                 out = h_out[:s.numel()]
                 out.copy_(s)
             else:
-                y = falcon.decompress(d_in[:nb], out=d_out.view(torch.float64 if payload[5] == falcon.F64
-                                                                else torch.float32), stream=stream)
+                y = falcon.decompress(d_in[:nb], out=d_out.view(falcon.torch_dtype(int(payload[5]))), stream=stream)
                 out = h_out[:y.numel() * y.element_size()]
                 out.copy_(y.view(torch.uint8))
             lat.append(time.perf_counter() - t0 - t)

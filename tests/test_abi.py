@@ -34,10 +34,10 @@ def test_exports_every_declared_symbol(falcon_lib):
 
 def test_bound_matches_oracle(falcon_lib, oracle):
     for n in (0, 1, 2, 63, 64, 65, 1023, 1024, 1025, 1 << 20, 67108864):
-        for dt in (0, 1):
+        for dt in (0, 1, 2):
             for blk in (2, 64, 1000, 1024, 1025):
                 assert falcon_lib.bound(n, dt, blk) == oracle.bound(n, dt, blk), (n, dt, blk)
-    assert falcon_lib.bound(10, 2, 1024) == 0
+    assert falcon_lib.bound(10, 3, 1024) == 0 and oracle.bound(10, 3, 1024) == 0
     assert falcon_lib.bound(10, 0, 1) == 0
     for blk in (1026, 4096, 65537):                    # the format stops at n = 1025 (Sec. 3.3)
         assert falcon_lib.bound(10, 0, blk) == 0 and oracle.bound(10, 0, blk) == 0
