@@ -49,6 +49,7 @@ def parse_args():
     ap.add_argument("--no-pipeline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-case1", action="store_true")
+    ap.add_argument("--no-f16", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-schedulers", action="store_true")
     ap.add_argument("--no-sweeps", action="store_true")
@@ -60,8 +61,8 @@ def parse_args():
     ap.add_argument("--batch-series", type=int, default=4096, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.kernels_only:
-        for k in ("no_cpu_baseline", "no_e2e", "no_batched", "no_pipeline", "no_serve", "no_case1", "no_variants",
-                  "no_schedulers", "no_sweeps"):
+        for k in ("no_cpu_baseline", "no_e2e", "no_batched", "no_pipeline", "no_serve", "no_case1", "no_f16",
+                  "no_variants", "no_schedulers", "no_sweeps"):
             setattr(args, k, True)
     return args
 
@@ -518,6 +519,9 @@ def main():
     if rank == 0 and not args.no_case1:
         progress("case-1 workload")
         line["case1"] = bench_case1(falcon, torch, dev, n, peak)
+    if rank == 0 and not args.no_f16:
+        progress("fp16 workload")
+        line["f16"] = bench_f16(falcon, torch, dev, n, peak)
     if rank == 0 and not args.no_variants:
         progress("codec variants")
         line["variants"] = bench_variants(falcon, torch, dev, host)
@@ -942,6 +946,36 @@ def bench_case1(falcon, torch, dev, n, peak):
         out[f"case1_chunks_{name}"] = case1
         out[f"bit_exact_{name}"] = ok
         del x, st
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_f16(falcon, torch, dev, n, peak):
+    """Binary16 (R18) at HBM scale: 2^26 FP16 segment values (128 MiB), per-kernel time, roofline
+    fraction, ratio, share of Case-1 chunks; the stream checked against the oracle's on its
+    first 4096 chunks and decoded bit-exactly."""
+    from oracle import oracle
+    from paper_2511_04140_gb300 import synth
+    oracle.build()
+    arr = synth.segments_f16(n, seed=5)
+    x = torch.from_numpy(arr).to(dev)
+    tc, td, st, ok = time_codec(falcon, torch, x, BLOCK, reps=5)
+    nb = st.numel()
+    blob = st.cpu().numpy().tobytes()
+    nc = (n + BLOCK - 1) // BLOCK
+    sizes = np.frombuffer(blob, dtype="<u4", count=nc, offset=32)
+    offs = 32 + 4 * nc + np.concatenate([[0], np.cumsum(sizes[:-1], dtype=np.int64)])
+    alpha = np.frombuffer(blob, dtype=np.uint8)[offs]
+    out = {"workload": f"FP16 segments: {n} values (128 MiB), 4096-value segments with 0..2 places, amplitude "
+                       "10^U(-1,1), sinusoid + AR(1), 0.01% full-precision outliers, 0.001% specials; block 1024",
+           "kernels": {}, "ratio": nb / arr.nbytes, "case1_chunks": float(np.mean(alpha <= 4)), "bit_exact": ok,
+           "oracle_equal": oracle_equal_sampled(oracle, arr, blob, BLOCK),
+           "oracle_check": "the first 4096 chunks' records against the oracle's"}
+    for kind, ms in (("compress", tc), ("decompress", td)):
+        alg = arr.nbytes + nb
+        out["kernels"][f"{kind}_f16"] = {"ms": ms, "gbs_original": arr.nbytes / ms / 1e6, "hbm_gbs": alg / ms / 1e6,
+                                         "hbm_frac": alg / ms / 1e6 / peak}
+    del x, st
     torch.cuda.empty_cache()
     return out
 

@@ -1,7 +1,7 @@
 /*
  * falcon.h -- C ABI of libfalcon, a GB300 (sm_103a) implementation of the Falcon codec:
- * lossless, per-chunk compression of FP64 / FP32 series (Falcon: GPU-Based Floating-point
- * Adaptive Lossless Compression, arXiv 2511.04140).
+ * lossless, per-chunk compression of FP64 / FP32 / FP16 series (Falcon: GPU-Based
+ * Floating-point Adaptive Lossless Compression, arXiv 2511.04140).
  *
  * What one call computes (per chunk of block_size consecutive values):
  *   - the float-to-integer transform of Sec. 3.2 (Alg. 2 decimal place detection, Eq. 4:
@@ -10,23 +10,25 @@
  *   - delta + zigzag coding (Eq. 5);
  *   - the adaptive sparse/dense bit-plane encoding of Sec. 3.3 (Fig. 8);
  *   - the compressed-size synchronisation and chunk writing of Sec. 3.4 (Alg. 3): the record
- *     sizes, their exclusive prefix per stream, then every record written at its offset
- *     (three kernel launches on the caller's stream, none waiting on another warp);
+ *     sizes and their sums per 64- and 4096-chunk group, then every record written at its
+ *     offset (two kernel launches on the caller's stream, none waiting on another warp);
  * and decompression (Sec. 4) is its exact inverse.  FP32 follows the same steps with
- * alpha <= 10, beta <= 7 and 32-bit integers.
+ * alpha <= 10, beta <= 7 and 32-bit integers; FP16 (binary16, FALCON_F16; Sec. 2.1 extends
+ * the method to other precisions, this library fixes its constants) with alpha <= 4,
+ * beta <= 3, eps <= |x| 2^-10, 16-bit integers and fl16 round trips.
  *
  * Stream format (self-describing, little-endian):
- *   bytes 0..31   "FLCN", version u8 (=1), dtype u8, u16 0, block_size u32, u32 0,
+ *   bytes 0..31   "FLCN", version u8 (=1), dtype u8 (falcon_dtype), u16 0, block_size u32, u32 0,
  *                 n u64, num_chunks u64
  *   then          u32 size[num_chunks]  (compressed bytes of each chunk record)
  *   then          the chunk records back to back:
- *                 [alpha_max u8][beta_hat_max u8][z_1: 8 B (FP32: 4 B)][w u8]
+ *                 [alpha_max u8][beta_hat_max u8][z_1: 8 B (FP32: 4 B, FP16: 2 B)][w u8]
  *                 [flags: ceil(w/8) B, the last w bits = rows 1..w, 1 = dense]
  *                 [row 1 = bit plane w-1] ... [row w = bit plane 0]
  *   A sparse row is a bitmap of cols/64 bytes (bit 7 of byte 0 = row byte 0) followed by
  *   the row's non-zero bytes; a dense row is its cols/8 bytes; cols = round_up(m-1, 64)
  *   for a chunk of m values.  Case-2 records carry alpha_max = 23, beta_hat_max = 16
- *   (FP32: 11 and 8).
+ *   (FP32: 11 and 8; FP16: 5 and 4).
  *
  * Conventions for every entry point:
  *   - Return value: a falcon_status.  Nothing is thrown across the ABI.  On error the

@@ -158,6 +158,34 @@ def segments(n: int = 1 << 26, seed: int = 1, dtype=np.float64, seg_len: int = 4
     return vals
 
 
+def segments_f16(n: int = 1 << 26, seed: int = 1, seg_len: int = 4096, outlier_rate: float = 1e-4,
+                 special_rate: float = 1e-5) -> np.ndarray:
+    """Binary16 segments: the sinusoid + AR(1) construction with amplitude 10^U(-1, 1) and
+    U{0..2} places, rounded to binary16 (1 to 4 significant digits, so chunks of both Cases);
+    a few full-precision outliers and special values."""
+    from scipy.signal import lfilter
+
+    rng = np.random.default_rng(seed)
+    nseg = (n + seg_len - 1) // seg_len
+    places = rng.integers(0, 3, size=nseg)
+    amp = 10.0 ** rng.uniform(-1, 1, size=nseg)
+    period = rng.uniform(64, 4096, size=nseg)
+    phase = rng.uniform(0, 2 * np.pi, size=nseg)
+    seg = np.arange(n) // seg_len
+    t = (np.arange(n) % seg_len).astype(np.float64)
+    ar = lfilter([1.0], [1.0, -0.95], rng.standard_normal(n))
+    x = amp[seg] * np.sin(2 * np.pi * t / period[seg] + phase[seg]) + 0.01 * amp[seg] * ar
+    pl = places[seg]
+    vals = (np.rint(x * 10.0 ** pl) / 10.0 ** pl).astype(np.float16)
+    n_out = rng.binomial(n, outlier_rate)
+    pos = rng.choice(n, size=n_out, replace=False)
+    vals[pos] = (x[pos] * np.pi).astype(np.float16)
+    n_sp = rng.binomial(n, special_rate)
+    pos = rng.choice(n, size=n_sp, replace=False)
+    vals[pos] = np.array([np.nan, np.inf, -np.inf, -0.0, 6e-8], dtype=np.float16)[rng.integers(0, 5, n_sp)]
+    return vals
+
+
 def series_batch(count: int = 4096, seed: int = 2, min_len: int = 1024, max_len: int = 1 << 22,
                  p_f64: float = 0.7, max_outlier_rate: float = 0.05):
     """Independent series: length floor(2^U(log2 min, log2 max)), FP64 with probability
