@@ -193,8 +193,10 @@ __device__ __noinline__ int search_alpha(const uint8_t *buf, int lane, uint32_t 
 // |v| 10^k >= 2^(p-1) / 1.5 (p = 24 or 11 significand bits): with d / 10^k its shortest decimal,
 // v 10^a (a < k) lies at least 10^-(k-a) - |v| 10^a 2^-p from every integer, more than
 // mu = |v 10^a| 2^-(p-1) below that bound (checked exhaustively over every decimal below it).
-// k <= alpha, so a value can stop early only if 3 |v| 10^alpha >= 2^(p-1) (half the bound, as a
-// margin); only those values go through Alg. 2, and none when v_max is below.
+// k <= alpha, so a value can stop early only if |v| 10^alpha reaches the bound.  FP32 tests
+// 3 |v| 10^alpha >= 2^23 (half the bound, as a margin: the bound was checked exhaustively only
+// up to that point); FP16 tests the bound itself, 3 |v| 10^alpha >= 2^11, checked over all
+// 65,536 patterns.  Only those values go through Alg. 2, and none when v_max is below.
 __device__ __forceinline__ bool may_stop_early(uint32_t u, int a) {
     const uint32_t au = u & 0x7FFFFFFFu;
     if (au == 0) return false;
@@ -210,7 +212,7 @@ __device__ __forceinline__ bool may_stop_early(uint16_t u, int a) {
     if (au < 0x0400u) return true;
     const int E = (int)(au >> 10) - 25;
     const uint32_t p = 3u * ((au & 0x3FFu) | 0x400u) * (uint32_t)FALCON_POW5[a];     // < 2^22
-    const int s = 10 - E - a;                    // 3 m 5^a 2^(E+a) >= 2^10  <=>  p >= 2^s
+    const int s = 11 - E - a;                    // 3 m 5^a 2^(E+a) >= 2^11  <=>  p >= 2^s
     return s <= 0 || (s < 32 && p >= (1u << s));
 }
 __device__ __forceinline__ int first_pass(uint32_t u, int atop) { return first_pass_f32(u, atop); }

@@ -513,35 +513,6 @@ __device__ __forceinline__ uint16_t case1_g(uint16_t u, int a) {
     return (uint16_t)((u >> 15) ? (0u - N) : N);
 }
 
-// fl16(g / 10^a) (R18), correctly rounded, for |g| <= 2^15 and 0 <= a <= 4: the quotient by 5^a
-// as in div_pow10_exact below, rounded at 11 significant bits instead of 53 (the result is
-// normal: |g| / 10^a >= 10^-4).  Returns the binary16 pattern.
-__device__ __forceinline__ uint16_t div_pow10_h(int32_t g, int a) {
-    if (g == 0) return 0;
-    const uint32_t sign = g < 0 ? 0x8000u : 0u;
-    const uint64_t ag = g < 0 ? (uint64_t)(-(int64_t)g) : (uint64_t)g;
-    const int s = __clzll((long long)ag);
-    const uint64_t G = ag << s;
-    uint64_t T = G, r = 0;
-    int d = 0;
-    if (a > 0) {
-        d = FALCON_LOG2_POW5[a];
-        const uint64_t D = FALCON_POW5[a];
-        T = __umul64hi(G, FALCON_RECIP5[a]);
-        r = (G << d) - T * D;
-        if (r >= D) { r -= D; ++T; }
-    }
-    const int lz = __clzll((long long)T);
-    const uint64_t Tn = T << lz;
-    uint32_t mant = (uint32_t)(Tn >> 53);
-    const uint64_t rest = Tn & ((1ull << 53) - 1ull);
-    const bool sticky = (rest & ((1ull << 52) - 1ull)) != 0ull || r != 0;
-    if ((rest >> 52) && (sticky || (mant & 1u))) ++mant;
-    int e2 = 53 - lz - d - s - a;               // the value is mant * 2^e2
-    if (mant == 2048u) { mant = 1024u; ++e2; }
-    return (uint16_t)(sign | ((uint32_t)(e2 + 25) << 10) | (mant & 0x3FFu));
-}
-
 // fl(g / 10^a), correctly rounded (nearest, ties to even), for |g| < 2^53 and 0 <= a <= 22, in
 // integer arithmetic (the inverse of Eq. 4, Case 1).  g / 10^a = (g / 5^a) 2^-a and the
 // scaling by 2^-a is exact (no result is subnormal), so the work is one correctly rounded

@@ -74,6 +74,17 @@ def test_f16_div_pow10_correctly_rounded(oracle):
             assert oracle.f16_div_pow10(g, a) == nearest_half(Fraction(g, 10 ** a)), (g, a)
 
 
+def test_fp32_then_fp16_quotient_is_correctly_rounded(oracle):
+    """The GPU decodes FP16 Case 1 as fl16(fl32(g / 10^a)): for every 16-bit g and a <= 4 that
+    double rounding equals the correctly rounded fl16(g / 10^a) (numpy's FP32 division and
+    FP32 -> FP16 conversion are IEEE round-to-nearest-even)."""
+    g = np.arange(-32768, 32768, dtype=np.int64)
+    for a in range(5):
+        two_step = (g.astype(np.float32) / np.float32(10.0 ** a)).astype(np.float16).view(np.uint16)
+        exact = np.array([oracle.f16_div_pow10(int(x), a) for x in g], dtype=np.uint16)
+        assert np.array_equal(two_step, exact), a
+
+
 def test_special_f16_every_pattern(oracle):
     f = HALF.astype(np.float64)
     sub = (ALL & 0x7C00 == 0) & (ALL & 0x3FF != 0)
