@@ -50,6 +50,12 @@
  *       trip and the decode are fl16(g / 10^alpha), correctly rounded (ties to even); the
  *       Case-2 sentinels are (5, 4); zigzag and deltas are modulo 2^16; z_1 takes 2 bytes and
  *       w <= 16.  -0, NaN, +-inf and subnormals are exceptions (R1).
+ *   R19 analytics on compressed data (Sec. 7 names it as future work and fixes nothing): an
+ *       aggregate of a stream's values, count, number of NaNs, min and max of the other
+ *       values in IEEE 754 totalOrder (-0 < +0; NaN when there is none) and their sum, taken
+ *       from the records without writing the values out.  The oracle decompresses (Sec. 4)
+ *       and aggregates by the definition; its sum is the exact sum correctly rounded to FP64
+ *       (an inf of one sign gives that inf, both signs NaN).
  *   R17 the ablation variants of Sec. 5.4.2 (Fig. 12b) change one step each and keep the
  *       record layout, so the one decoder reads all of them:
  *         Fal._Sparse / Fal._Dense: every row of M^T stored sparse / dense;
@@ -1076,4 +1082,109 @@ int oracle_decompress_mt(const uint8_t *in, size_t in_bytes, void *out, size_t o
     free(offs);
     if (st == OR_OK) *n_out = n;
     return st;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* R19: aggregate of a stream's values, by decompressing it (Sec. 4) and applying the     */
+/* definition.  The sum of the non-NaN values is exact, then rounded once: the values are */
+/* kept as a list of non-overlapping FP64 partials whose exact sum is the running total  */
+/* (each addition split into its rounded sum and its error by the two-sum of Knuth, TAOCP */
+/* Vol. 2, 4.2.2; the partial list as in Shewchuk, "Adaptive Precision Floating-Point    */
+/* Arithmetic", 1997), and the partials are added once at the end with the rounding      */
+/* corrected (half-way cases resolved by the next partial).                              */
+/* ------------------------------------------------------------------------------------ */
+typedef struct {
+    double *p;
+    size_t n, cap;
+} exact_sum;
+
+static void exact_add(exact_sum *s, double x)
+{
+    size_t k = 0;
+    for (size_t i = 0; i < s->n; ++i) {
+        double y = s->p[i];
+        if (fabs(x) < fabs(y)) { double t = x; x = y; y = t; }
+        const double hi = x + y;
+        const double lo = y - (hi - x);                /* exact, |x| >= |y| */
+        if (lo != 0.0) s->p[k++] = lo;
+        x = hi;
+    }
+    if (k >= s->cap) {
+        s->cap = 2 * s->cap + 8;
+        s->p = (double *)realloc(s->p, sizeof(double) * s->cap);
+    }
+    s->p[k++] = x;
+    s->n = k;
+}
+
+static double exact_result(const exact_sum *s)
+{
+    if (s->n == 0) return 0.0;
+    size_t i = s->n - 1;
+    double hi = s->p[i], lo = 0.0;
+    while (i > 0) {
+        const double x = hi, y = s->p[--i];
+        hi = x + y;
+        const double yr = hi - x;
+        lo = y - yr;
+        if (lo != 0.0) break;
+    }
+    /* the rounding of hi is exact to half an ulp; a half-way case with more partials below
+       of the same sign as lo rounds away from hi */
+    if (i > 0 && ((lo < 0.0 && s->p[i - 1] < 0.0) || (lo > 0.0 && s->p[i - 1] > 0.0))) {
+        const double y = lo * 2.0, x = hi + y, yr = x - hi;
+        if (y == yr) hi = x;
+    }
+    return hi;
+}
+
+static uint64_t total_order_key(double v)
+{
+    const uint64_t b = bits64(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+int oracle_aggregate(const uint8_t *in, size_t in_bytes, uint64_t *count, uint64_t *nan_count, double *vmin,
+                     double *vmax, double *sum)
+{
+    uint64_t n, nc;
+    int dtype;
+    uint32_t block;
+    int st = oracle_stream_info(in, in_bytes, &n, &dtype, &block, &nc);
+    if (st != OR_OK) return st;
+    const size_t s = elem_size(dtype);
+    uint8_t *vals = (uint8_t *)malloc(n ? n * s : 1);
+    if (!vals) return OR_ERR_CAPACITY;
+    uint64_t got = 0;
+    st = oracle_decompress(in, in_bytes, vals, n * s, &got);
+    if (st != OR_OK) { free(vals); return st; }
+    exact_sum es = {NULL, 0, 0};
+    uint64_t nans = 0, kmin = 0, kmax = 0;
+    int any = 0, pinf = 0, ninf = 0;
+    double lo = NAN, hi = NAN;
+    for (uint64_t i = 0; i < n; ++i) {
+        double v;
+        if (dtype == OR_F64) { memcpy(&v, vals + 8 * i, 8); }
+        else if (dtype == OR_F32) { float f; memcpy(&f, vals + 4 * i, 4); v = (double)f; }
+        else { uint16_t h; memcpy(&h, vals + 2 * i, 2); v = oracle_half_to_double(h); }
+        if (isnan(v)) { ++nans; continue; }
+        const uint64_t k = total_order_key(v);
+        if (!any || k < kmin) { kmin = k; lo = v; }
+        if (!any || k > kmax) { kmax = k; hi = v; }
+        any = 1;
+        if (isinf(v)) { if (v > 0) pinf = 1; else ninf = 1; }
+        else exact_add(&es, v);
+    }
+    double total = exact_result(&es);
+    if (pinf && ninf) total = NAN;
+    else if (pinf) total = INFINITY;
+    else if (ninf) total = -INFINITY;
+    free(es.p);
+    free(vals);
+    *count = n;
+    *nan_count = nans;
+    *vmin = lo;
+    *vmax = hi;
+    *sum = total;
+    return OR_OK;
 }

@@ -92,6 +92,8 @@ def lib():
             L.oracle_floor_log10_f16.argtypes = [c.c_uint16]
             L.oracle_dp_ds_f16.argtypes = [c.c_uint16, c.POINTER(c.c_int), c.POINTER(c.c_int)]
             L.oracle_dp_elf_f16.argtypes = [c.c_uint16, c.POINTER(c.c_int), c.POINTER(c.c_int)]
+            L.oracle_aggregate.argtypes = [c.c_void_p, c.c_size_t, c.POINTER(c.c_uint64), c.POINTER(c.c_uint64),
+                                           c.POINTER(c.c_double), c.POINTER(c.c_double), c.POINTER(c.c_double)]
             L.oracle_chunk_transform.argtypes = [c.c_void_p, c.c_uint32, c.c_int,
                                                  c.POINTER(c.c_int), c.POINTER(c.c_int),
                                                  c.POINTER(c.c_int), c.c_void_p]
@@ -361,3 +363,16 @@ def chunk_records(stream: bytes):
         recs.append(stream[pos:pos + int(s)])
         pos += int(s)
     return recs
+
+
+def aggregate(stream: bytes) -> dict:
+    """R19's aggregate of a stream: count, nan_count, min / max in totalOrder (NaN if none),
+    and the correctly rounded exact sum of the non-NaN values."""
+    buf = np.frombuffer(stream, dtype=np.uint8)
+    cnt, nan = ctypes.c_uint64(), ctypes.c_uint64()
+    lo, hi, sm = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    st = lib().oracle_aggregate(_ptr(buf), len(buf), ctypes.byref(cnt), ctypes.byref(nan), ctypes.byref(lo),
+                                ctypes.byref(hi), ctypes.byref(sm))
+    if st != OK:
+        raise ValueError(f"oracle_aggregate status {st}")
+    return {"count": cnt.value, "nan_count": nan.value, "min": lo.value, "max": hi.value, "sum": sm.value}
