@@ -130,6 +130,42 @@ int falcon_decompress_async(const void *d_in, size_t in_bytes, const void *h_hea
                             size_t workspace_bytes, uint64_t *d_result, void *stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Analytics on compressed data (Sec. 7 names it as future work and fixes nothing; this
+ * library's reading): an aggregate of a stream's values computed from its records on the
+ * GPU, the records decoded in registers and never written out as values.
+ *   count      number of values (n of the header);
+ *   nan_count  number of NaN values;
+ *   min, max   smallest / largest non-NaN value in IEEE 754 totalOrder (-0 < +0), widened
+ *              exactly to FP64; NaN when every value is a NaN or the stream is empty;
+ *   sum        sum of the non-NaN values in FP64: each 32-value group in index order, then
+ *              fixed trees over groups, chunks and the stream, so the result is reproducible;
+ *              within depth * 2^-53 * sum(|x|) of the exact sum (depth: the additions on
+ *              any path, 38 + ceil(chunks / 1024) + 10); +0 when there is no non-NaN value;
+ *   status     falcon_status of the device-side work (FALCON_ERR_CORRUPT for a malformed
+ *              record).
+ */
+typedef struct {
+    uint64_t count;
+    uint64_t nan_count;
+    double min;
+    double max;
+    double sum;
+    uint64_t status;
+} falcon_stats;
+
+/* Asynchronous aggregate of the stream at d_in (device, in_bytes; h_header a host copy of
+ * its first 32 bytes) into d_stats (device, one falcon_stats).  d_workspace:
+ * falcon_workspace_bytes(number of chunks) bytes of 256-byte aligned device memory owned by
+ * the caller.  Enqueues four launches on `stream` and returns without synchronising
+ * (capturable).  Errors as falcon_decompress_async. */
+int falcon_aggregate_async(const void *d_in, size_t in_bytes, const void *h_header, void *d_workspace,
+                           size_t workspace_bytes, falcon_stats *d_stats, void *stream);
+
+/* Synchronous form: reads the header back, uses the library's cached workspace, copies the
+ * result to *h_stats (host) and returns its status. */
+int falcon_aggregate(const void *d_in, size_t in_bytes, falcon_stats *h_stats, void *stream);
+
+/* ---------------------------------------------------------------------------------------
  * Codec variants: Falcon and the three ablations of Sec. 5.4.2 (Fig. 12b).  Each changes one
  * step and keeps the record layout, so falcon_decompress reads every variant's streams:
  *   FALCON_VARIANT_FALCON  the method itself (what falcon_compress writes);

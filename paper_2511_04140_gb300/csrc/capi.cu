@@ -319,6 +319,53 @@ int falcon_decompress_async(const void *d_in, size_t in_bytes, const void *h_hea
     return FALCON_OK;
 }
 
+int falcon_aggregate_async(const void *d_in, size_t in_bytes, const void *h_header, void *d_workspace,
+                           size_t workspace_bytes, falcon_stats *d_stats, void *stream) {
+    if (!d_in || !h_header) return FALCON_ERR_INVALID;
+    if (in_bytes < FALCON_HEADER_BYTES) return FALCON_ERR_CORRUPT;
+    Header h;
+    int st = parse_header(static_cast<const uint8_t *>(h_header), FALCON_HEADER_BYTES, &h);
+    if (st) return st;
+    if ((uintptr_t)d_in % 16 != 0) return FALCON_ERR_INVALID;
+    if (h.nchunks > (in_bytes - FALCON_HEADER_BYTES) / 4) return FALCON_ERR_CORRUPT;
+    const size_t need = falcon_workspace_bytes(h.nchunks);
+    if (!d_workspace || !d_stats || workspace_bytes < need || (uintptr_t)d_workspace % 256 != 0 ||
+        (uintptr_t)d_stats % 8 != 0)
+        return FALCON_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_workspace, 0, need, s) != cudaSuccess) return FALCON_ERR_CUDA;
+    uint8_t *w8 = static_cast<uint8_t *>(d_workspace);
+    // no values are stored: the job has no output; its status word sits in the control region
+    uint64_t *result = reinterpret_cast<uint64_t *>(w8 + kResultOffset);
+    const Job j = make_decompress_job(d_in, in_bytes, h, nullptr, 0, w8 + kControlBytes, result);
+    if (launch_aggregate(j, reinterpret_cast<Control *>(d_workspace), d_stats, s) != cudaSuccess)
+        return FALCON_ERR_CUDA;
+    return FALCON_OK;
+}
+
+int falcon_aggregate(const void *d_in, size_t in_bytes, falcon_stats *h_stats, void *stream) {
+    if (!d_in || !h_stats) return FALCON_ERR_INVALID;
+    if ((uintptr_t)d_in % 16 != 0) return FALCON_ERR_INVALID;
+    if (in_bytes < FALCON_HEADER_BYTES) return FALCON_ERR_CORRUPT;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint8_t hdr[FALCON_HEADER_BYTES];
+    if (cudaMemcpyAsync(hdr, d_in, sizeof hdr, cudaMemcpyDeviceToHost, s) != cudaSuccess) return FALCON_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FALCON_ERR_CUDA;
+    Header h;
+    int st = parse_header(hdr, sizeof hdr, &h);
+    if (st) return st;
+    // the workspace, then one falcon_stats after it, in the cached buffer
+    const size_t ws_bytes = falcon_workspace_bytes(h.nchunks);
+    void *ws = nullptr;
+    if ((st = get_workspace(s, ws_bytes + 256, &ws))) return st;
+    falcon_stats *d_stats = reinterpret_cast<falcon_stats *>(static_cast<uint8_t *>(ws) + ws_bytes);
+    if ((st = falcon_aggregate_async(d_in, in_bytes, hdr, ws, ws_bytes, d_stats, stream))) return st;
+    if (cudaMemcpyAsync(h_stats, d_stats, sizeof(falcon_stats), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FALCON_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FALCON_ERR_CUDA;
+    return (int)h_stats->status;
+}
+
 int falcon_release(void) {
     std::lock_guard<std::mutex> lk(g_mu);
     int cur = 0;

@@ -16,6 +16,7 @@
 //      c. values are staged (swizzled) and written with coalesced 16-byte stores.
 // Every read of a record is bounds-checked against its size; a malformed record sets
 // FALCON_ERR_CORRUPT and writes nothing.
+#include "falcon.h"
 #include "falcon_device.cuh"
 
 namespace falcon {
@@ -149,9 +150,22 @@ __device__ __forceinline__ void copy_to_planes(uint8_t *dst, const uint8_t *src,
 
 // `next` starts the copy of the warp's next record into rbuf; it is called exactly once, as
 // soon as this record has been read completely.
-template <int D, class Next>
+// A value's exact FP64 value, and its key in IEEE 754 totalOrder (for min / max of non-NaN values).
+__device__ __forceinline__ double value_f64(uint64_t b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ double value_f64(uint32_t b) { return (double)__uint_as_float(b); }
+__device__ __forceinline__ double value_f64(uint16_t b) { return (double)__half2float(__ushort_as_half(b)); }
+__device__ __forceinline__ uint64_t order_key(double x) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// kAgg (analytics on compressed data): instead of storing the values, the warp adds them up
+// (NaN count, totalOrder min / max, their sum: each lane its 32 values in index order, then a
+// butterfly over the lanes, identical in every lane since FP addition commutes); the chunk's
+// sum goes to sums[c], the rest into the control block by atomics.
+template <int D, bool kAgg, class Next>
 __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const uint8_t *rbuf, uint8_t *pbuf,
-                             int lane, Next &&next) {
+                             int lane, Next &&next, Control *ctl) {
     using T = Traits<D>;
     using U = typename T::U;
 
@@ -357,6 +371,39 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     d[0] = carry;
     __syncwarp();                                 // plane words consumed
 
+    if constexpr (kAgg) {
+        uint32_t nan = 0;
+        uint64_t kmin = ~0ull, kmax = 0;
+        double sum = -0.0;                        // -0 + x == x for every x, -0 + -0 == -0
+        auto take = [&](U b) {
+            const double x = value_f64(b);
+            if (x != x) { ++nan; return; }
+            const uint64_t key = order_key(x);
+            kmin = key < kmin ? key : kmin;
+            kmax = key > kmax ? key : kmax;
+            sum = __dadd_rn(sum, x);
+        };
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            if (32u * (uint32_t)lane + (uint32_t)k < m) take(d[k]);
+        if (m > 1024u && lane == 31) take(vx);
+        nan = __reduce_add_sync(kFull, nan);
+        kmin = ~warp_max_u64(~kmin);
+        kmax = warp_max_u64(kmax);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum = __dadd_rn(sum, __shfl_xor_sync(kFull, sum, o));
+        if (lane == 0) {
+            reinterpret_cast<double *>(job.flags + tile_count(job.nchunks))[c] = sum;
+            if (nan) atomicAdd(&ctl->agg[0], (unsigned long long)nan);
+            if (kmax) {                           // some value was not a NaN
+                atomicMax(&ctl->agg[1], (unsigned long long)~kmin);
+                atomicMax(&ctl->agg[2], (unsigned long long)kmax);
+            }
+        }
+        __syncwarp();
+        return;
+    }
+
     // ---- c. stage (swizzled) and store --------------------------------------------------------
     constexpr int UN = T::UNITS;
 #pragma unroll
@@ -405,7 +452,7 @@ constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2, kDtF16 = 3;
 // the value kind whose buffers a form needs (the either-dtype form: the largest)
 template <int kDt> constexpr int layout_kind() { return kDt == kDtF32 ? kD32 : (kDt == kDtF16 ? kD16 : kD64); }
 
-template <int kDt>
+template <int kDt, bool kAgg = false>
 __global__ void __launch_bounds__(32 * kMaxDecompressWarps, 1)
 decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -452,12 +499,12 @@ decompress_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t 
             cp_async_commit();
         };
         const Job &job = job_of(jobs, njobs, s_single, t);
-        if constexpr (kDt == kDtF64) decode_chunk<kD64>(job, lc, okc, wbase, pbuf, lane, next);
-        else if constexpr (kDt == kDtF32) decode_chunk<kD32>(job, lc, okc, wbase, pbuf, lane, next);
-        else if constexpr (kDt == kDtF16) decode_chunk<kD16>(job, lc, okc, wbase, pbuf, lane, next);
-        else if (job.dtype == 0) decode_chunk<kD64>(job, lc, okc, wbase, pbuf, lane, next);
-        else if (job.dtype == 1) decode_chunk<kD32>(job, lc, okc, wbase, pbuf, lane, next);
-        else decode_chunk<kD16>(job, lc, okc, wbase, pbuf, lane, next);
+        if constexpr (kDt == kDtF64) decode_chunk<kD64, kAgg>(job, lc, okc, wbase, pbuf, lane, next, ctl);
+        else if constexpr (kDt == kDtF32) decode_chunk<kD32, kAgg>(job, lc, okc, wbase, pbuf, lane, next, ctl);
+        else if constexpr (kDt == kDtF16) decode_chunk<kD16, kAgg>(job, lc, okc, wbase, pbuf, lane, next, ctl);
+        else if (job.dtype == 0) decode_chunk<kD64, kAgg>(job, lc, okc, wbase, pbuf, lane, next, ctl);
+        else if (job.dtype == 1) decode_chunk<kD32, kAgg>(job, lc, okc, wbase, pbuf, lane, next, ctl);
+        else decode_chunk<kD16, kAgg>(job, lc, okc, wbase, pbuf, lane, next, ctl);
         if (tn >= total_chunks) break;
         t = tn;
         tn = tnn;
@@ -475,16 +522,59 @@ int decompress_grid(uint64_t total_chunks) {
                                 g_ctas_per_sm[1], total_chunks);
 }
 
+// The aggregate's last step (one CTA): thread t adds the chunk sums of its contiguous share in
+// chunk order, then a fixed tree over the threads; the NaN count and the min / max keys come
+// from the control block, the status from the decode.  Every step has a fixed order, so the
+// result does not depend on the schedule.
+__global__ void __launch_bounds__(1024)
+aggregate_finish_kernel(Job single, Control *ctl, falcon_stats *out) {
+    __shared__ double part[1024];
+    const uint64_t nc = single.nchunks;
+    const double *sums = reinterpret_cast<const double *>(single.flags + tile_count(nc));
+    const uint64_t c0 = nc * threadIdx.x / 1024u, c1 = nc * (threadIdx.x + 1u) / 1024u;
+    double s = -0.0;
+    for (uint64_t c = c0; c < c1; ++c) s = __dadd_rn(s, sums[c]);
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (unsigned h = 512; h > 0; h >>= 1) {
+        if (threadIdx.x < h) part[threadIdx.x] = __dadd_rn(part[threadIdx.x], part[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned long long nan = ctl->agg[0], kmin_c = ctl->agg[1], kmax = ctl->agg[2];
+        auto from_key = [](uint64_t k) {
+            return __longlong_as_double((long long)((k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k));
+        };
+        out->count = single.n;
+        out->nan_count = nan;
+        out->min = kmax ? from_key(~kmin_c) : __longlong_as_double(0x7FF8000000000000ll);
+        out->max = kmax ? from_key(kmax) : __longlong_as_double(0x7FF8000000000000ll);
+        out->sum = kmax ? part[0] : 0.0;          // no non-NaN value: the empty sum
+        out->status = single.result[1];
+    }
+}
+
 namespace {
-template <int kDt>
+template <int kDt, bool kAgg = false>
 void launch_decode(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
                    cudaStream_t stream) {
     const int w = g_cta_warps[1], smem = w * DecLayout<layout_kind<kDt>()>::kWarpBytes;
-    const int grid = persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDt>), w, smem,
+    const int grid = persistent_grid_size(reinterpret_cast<const void *>(decompress_kernel<kDt, kAgg>), w, smem,
                                           g_ctas_per_sm[1], total_chunks);
-    decompress_kernel<kDt><<<grid, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+    decompress_kernel<kDt, kAgg><<<grid, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
 }
 }  // namespace
+
+cudaError_t launch_aggregate(const Job &single, Control *ctl, void *d_stats, cudaStream_t stream) {
+    offsets_kernel<<<1, 1024, 0, stream>>>(nullptr, single);
+    if (single.nchunks > 0) {
+        if (single.dtype == 0) launch_decode<kDtF64, true>(nullptr, 1, single, single.nchunks, ctl, stream);
+        else if (single.dtype == 1) launch_decode<kDtF32, true>(nullptr, 1, single, single.nchunks, ctl, stream);
+        else launch_decode<kDtF16, true>(nullptr, 1, single, single.nchunks, ctl, stream);
+    }
+    aggregate_finish_kernel<<<1, 1024, 0, stream>>>(single, ctl, static_cast<falcon_stats *>(d_stats));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_decompress(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks,
                               Control *ctl, cudaStream_t stream) {

@@ -45,10 +45,12 @@ enum : uint32_t { kVariantFalcon = 0, kVariantSparse = 1, kVariantDense = 2, kVa
 // the chunk tickets of the persistent kernels.  A warp takes its next chunk with one atomic
 // add on its kernel's counter (analysis, emit, decode), so warps that met cheaper chunks take
 // more of them and a launch ends with its average warp, not its unluckiest one.
+// agg[] holds the aggregate launch's running values (analytics on compressed data): the NaN
+// count, the largest complement of a min key, the largest max key (zero: none yet).
 enum { kTicketAnalyse = 0, kTicketEmit = 1, kTicketDecode = 2 };
 struct Control {
     unsigned long long ticket[4];
-    unsigned int pad[8];
+    unsigned long long agg[4];
 };
 static_assert(sizeof(Control) == 64, "control block is 64 bytes");
 
@@ -74,6 +76,9 @@ cudaError_t launch_compress(const Job *d_jobs, int njobs, const Job &single,
                             uint64_t total_chunks, Control *ctl, cudaStream_t stream);
 cudaError_t launch_decompress(const Job *d_jobs, int njobs, const Job &single,
                               uint64_t total_chunks, Control *ctl, cudaStream_t stream);
+// analytics on compressed data: the decode without the stores, then the aggregate into
+// d_stats (falcon_stats); the chunk sums go into job.flags after the tile offsets
+cudaError_t launch_aggregate(const Job &single, Control *ctl, void *d_stats, cudaStream_t stream);
 
 // Status of the arguments of a compression call (dtype, block size, pointers, alignment,
 // room for the header and size array), checked before anything is enqueued.

@@ -88,6 +88,10 @@ def _load():
             L.falcon_variant_bound.argtypes = [u64, ci, u32, ci]
             L.falcon_decompress_async.restype = ci
             L.falcon_decompress_async.argtypes = [vp, sz, vp, vp, sz, vp, sz, vp, vp]
+            L.falcon_aggregate_async.restype = ci
+            L.falcon_aggregate_async.argtypes = [vp, sz, vp, vp, sz, vp, vp]
+            L.falcon_aggregate.restype = ci
+            L.falcon_aggregate.argtypes = [vp, sz, c.POINTER(Stats), vp]
             L.falcon_release.restype = ci
             L.falcon_batch_workspace_bytes.restype = sz
             L.falcon_batch_workspace_bytes.argtypes = [ci, c.POINTER(Series), ci]
@@ -207,6 +211,40 @@ def decompress(s: torch.Tensor, out: torch.Tensor | None = None, stream=None) ->
     _check(_load().falcon_decompress(s.data_ptr(), s.numel(), out.data_ptr(), out.numel() * out.element_size(),
                                      ctypes.byref(n_out), _stream_ptr(stream)), "decompress")
     return out[:n_out.value]
+
+
+class Stats(ctypes.Structure):
+    """falcon_stats: the aggregate of a stream (analytics on compressed data)."""
+    _fields_ = [("count", ctypes.c_uint64), ("nan_count", ctypes.c_uint64), ("min", ctypes.c_double),
+                ("max", ctypes.c_double), ("sum", ctypes.c_double), ("status", ctypes.c_uint64)]
+
+
+STATS_BYTES = 48
+
+
+def aggregate(s: torch.Tensor, stream=None) -> dict:
+    """Aggregate of the stream in a uint8 CUDA tensor, computed from its records without
+    writing the values: count, nan_count, min / max (totalOrder, non-NaN), sum."""
+    if not s.is_cuda or s.dtype != torch.uint8:
+        raise ValueError("s must be a uint8 CUDA tensor")
+    st = Stats()
+    _check(_load().falcon_aggregate(s.data_ptr(), s.numel(), ctypes.byref(st), _stream_ptr(stream)), "aggregate")
+    return {"count": st.count, "nan_count": st.nan_count, "min": st.min, "max": st.max, "sum": st.sum}
+
+
+def aggregate_async(s: torch.Tensor, nbytes: int, header: bytes, workspace: torch.Tensor, stats: torch.Tensor,
+                    stream=None) -> None:
+    """Enqueues the aggregate of s[:nbytes] into stats (uint8 CUDA tensor of STATS_BYTES,
+    8-byte aligned; read it with stats_of)."""
+    hdr = bytes(header)[:HEADER_BYTES]
+    _check(_load().falcon_aggregate_async(s.data_ptr(), nbytes, hdr, workspace.data_ptr(), workspace.numel(),
+                                          stats.data_ptr(), _stream_ptr(stream)), "aggregate_async")
+
+
+def stats_of(stats: torch.Tensor) -> dict:
+    st = Stats.from_buffer_copy(stats.cpu().numpy().tobytes())
+    return {"count": st.count, "nan_count": st.nan_count, "min": st.min, "max": st.max, "sum": st.sum,
+            "status": st.status}
 
 
 def compress_async(x: torch.Tensor, block: int, out: torch.Tensor, workspace: torch.Tensor,
