@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-case1", action="store_true")
     ap.add_argument("--no-f16", action="store_true")
+    ap.add_argument("--no-analytics", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-schedulers", action="store_true")
     ap.add_argument("--no-sweeps", action="store_true")
@@ -62,7 +63,7 @@ def parse_args():
     args = ap.parse_args()
     if args.kernels_only:
         for k in ("no_cpu_baseline", "no_e2e", "no_batched", "no_pipeline", "no_serve", "no_case1", "no_f16",
-                  "no_variants", "no_schedulers", "no_sweeps"):
+                  "no_analytics", "no_variants", "no_schedulers", "no_sweeps"):
             setattr(args, k, True)
     return args
 
@@ -522,6 +523,9 @@ def main():
     if rank == 0 and not args.no_f16:
         progress("fp16 workload")
         line["f16"] = bench_f16(falcon, torch, dev, n, peak)
+    if rank == 0 and not args.no_analytics:
+        progress("analytics on compressed data")
+        line["analytics"] = bench_analytics(falcon, torch, dev, host, peak)
     if rank == 0 and not args.no_variants:
         progress("codec variants")
         line["variants"] = bench_variants(falcon, torch, dev, host)
@@ -593,12 +597,13 @@ def section_main(args):
 
 
 def failed_checks(obj, path="line"):
-    """Paths of every false `bit_exact` / `oracle_equal` key in the bench line: a lossless
-    codec that lost a bit, or a stream that differs from the oracle's, fails the run."""
+    """Paths of every false `bit_exact` / `oracle_equal` / `equal_to_decompress_and_reduce` key
+    in the bench line: a lossless codec that lost a bit, a stream that differs from the
+    oracle's, or an aggregate that differs from the decompressed values' fails the run."""
     bad = []
     if isinstance(obj, dict):
         for k, v in obj.items():
-            if k in ("bit_exact", "oracle_equal") and v is False:
+            if k in ("bit_exact", "oracle_equal", "equal_to_decompress_and_reduce") and v is False:
                 bad.append(f"{path}.{k}")
             else:
                 bad += failed_checks(v, f"{path}.{k}")
@@ -977,6 +982,66 @@ def bench_f16(falcon, torch, dev, n, peak):
                                          "hbm_frac": alg / ms / 1e6 / peak}
     del x, st
     torch.cuda.empty_cache()
+    return out
+
+
+def bench_analytics(falcon, torch, dev, host, peak):
+    """Analytics on compressed data (R19): the aggregate (count, NaN count, min, max, sum) of the
+    2^26-value segment streams computed from the records, against decompressing them and
+    reducing the values with torch (nanmin/nanmax/nansum-style masked reductions); both timed
+    with CUDA events, inputs resident; results compared (count, NaNs, min/max exactly)."""
+    out = {"workload": "segment streams of 2^26 values (FP64 and FP32); aggregate = count, NaN count, "
+                       "totalOrder min / max and FP64 sum of the non-NaN values", "dtypes": {}}
+    stream = torch.cuda.current_stream(dev)
+    for dt, name in ((np.float64, "f64"), (np.float32, "f32")):
+        x = torch.from_numpy(host[dt]).to(dev)
+        s = falcon.compress(x, BLOCK)
+        nb = s.numel()
+        nc = (x.numel() + BLOCK - 1) // BLOCK
+        hdr = s[:32].cpu().numpy().tobytes()
+        ws = torch.zeros(falcon.workspace_bytes(nc), dtype=torch.uint8, device=dev)
+        st = torch.zeros(falcon.STATS_BYTES, dtype=torch.uint8, device=dev)
+        y = torch.empty_like(x)
+        rd = torch.zeros(2, dtype=torch.int64, device=dev)
+
+        def agg():
+            falcon.aggregate_async(s, nb, hdr, ws, st, stream)
+
+        def dec_reduce():
+            falcon.decompress_async(s, nb, hdr, y, ws, rd, stream)
+            m = torch.isnan(y)
+            v = y.masked_fill(m, 0.0)
+            return (m.sum(), v.to(torch.float64).sum(), y.masked_fill(m, float("inf")).min(),
+                    y.masked_fill(m, float("-inf")).max())
+
+        times = {}
+        for key, fn in (("aggregate", agg), ("decompress_and_reduce", dec_reduce)):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize(dev)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ms = []
+            for _ in range(10):
+                ev[0].record(stream)
+                fn()
+                ev[1].record(stream)
+                torch.cuda.synchronize(dev)
+                ms.append(ev[0].elapsed_time(ev[1]))
+            times[key] = float(np.median(ms))
+        a = falcon.stats_of(st)
+        nans, _, vmin, vmax = dec_reduce()
+        torch.cuda.synchronize(dev)
+        same = (a["status"] == 0 and a["count"] == x.numel() and a["nan_count"] == int(nans)
+                and a["min"] == float(vmin) and a["max"] == float(vmax))
+        orig = x.numel() * x.element_size()
+        out["dtypes"][name] = {
+            "aggregate_ms": times["aggregate"], "decompress_and_reduce_ms": times["decompress_and_reduce"],
+            "speedup": times["decompress_and_reduce"] / times["aggregate"],
+            "aggregate_gbs_original": orig / times["aggregate"] / 1e6,
+            "aggregate_hbm_frac": nb / times["aggregate"] / 1e6 / peak,
+            "equal_to_decompress_and_reduce": bool(same)}
+        del x, s, ws, y
+        torch.cuda.empty_cache()
     return out
 
 
