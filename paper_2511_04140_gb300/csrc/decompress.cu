@@ -372,32 +372,42 @@ __device__ void decode_chunk(const Job &job, const Loc &l, bool loc_ok, const ui
     __syncwarp();                                 // plane words consumed
 
     if constexpr (kAgg) {
+        // keys in the values' own width (IEEE order = unsigned order of the keys), widened to
+        // FP64 keys once per chunk
+        constexpr U SIGN = (U)((U)1 << (T::W - 1));
+        constexpr U ABSM = (U)(SIGN - 1u);
+        constexpr U INF = (U)(D == kD64 ? 0x7FF0000000000000ull : (D == kD32 ? 0x7F800000ull : 0x7C00ull));
         uint32_t nan = 0;
-        uint64_t kmin = ~0ull, kmax = 0;
+        U kmin = (U)~(U)0, kmax = 0;
         double sum = -0.0;                        // -0 + x == x for every x, -0 + -0 == -0
         auto take = [&](U b) {
-            const double x = value_f64(b);
-            if (x != x) { ++nan; return; }
-            const uint64_t key = order_key(x);
+            if ((U)(b & ABSM) > INF) { ++nan; return; }
+            const U key = (b & SIGN) ? (U)~b : (U)(b | SIGN);
             kmin = key < kmin ? key : kmin;
             kmax = key > kmax ? key : kmax;
-            sum = __dadd_rn(sum, x);
+            sum = __dadd_rn(sum, value_f64(b));
         };
 #pragma unroll
         for (int k = 0; k < 32; ++k)
             if (32u * (uint32_t)lane + (uint32_t)k < m) take(d[k]);
         if (m > 1024u && lane == 31) take(vx);
         nan = __reduce_add_sync(kFull, nan);
-        kmin = ~warp_max_u64(~kmin);
-        kmax = warp_max_u64(kmax);
+        if constexpr (D == kD64) {
+            kmin = ~warp_max_u64(~kmin);
+            kmax = warp_max_u64(kmax);
+        } else {
+            kmin = (U)__reduce_min_sync(kFull, (uint32_t)kmin);
+            kmax = (U)__reduce_max_sync(kFull, (uint32_t)kmax);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum = __dadd_rn(sum, __shfl_xor_sync(kFull, sum, o));
         if (lane == 0) {
             reinterpret_cast<double *>(job.flags + tile_count(job.nchunks))[c] = sum;
             if (nan) atomicAdd(&ctl->agg[0], (unsigned long long)nan);
             if (kmax) {                           // some value was not a NaN
-                atomicMax(&ctl->agg[1], (unsigned long long)~kmin);
-                atomicMax(&ctl->agg[2], (unsigned long long)kmax);
+                auto unkey = [&](U k) { return (k & SIGN) ? (U)(k & ABSM) : (U)~k; };
+                atomicMax(&ctl->agg[1], (unsigned long long)~order_key(value_f64(unkey(kmin))));
+                atomicMax(&ctl->agg[2], (unsigned long long)order_key(value_f64(unkey(kmax))));
             }
         }
         __syncwarp();
