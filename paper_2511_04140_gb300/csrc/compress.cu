@@ -472,29 +472,26 @@ __device__ void analyse_chunk(const Job &job, uint64_t c, const uint8_t *buf, ui
     // This lane's four bytes of row p cover its columns 8i .. 8i + 7 (i = 0..3); byte i is
     // non-zero iff bit p is set in o[i], the OR of those columns' Z.  The four bits of every
     // plane are added bit-sliced (count = b0 + 2 b1 + 4 b2) and spread into byte fields,
-    // planes 4g .. 4g + 3 in the bytes of packed[g].
+    // planes 4g .. 4g + 3 in the bytes of one word, which is added over the warp and stored, one
+    // g at a time (a rolled loop: its code stays small).
     const uint32_t cols = chunk_cols(m);
     const uint32_t row_bytes = cols / 8u;
     constexpr int PW = T::W < 32 ? 32 : T::W;  // planes the 32-bit words hold (FP16: 16 of them zero)
-    uint32_t packed[PW / 4];
-    {
 #pragma unroll
-        for (int h = 0; h < PW / 32; ++h) {
-            const uint32_t o0 = (uint32_t)((uint64_t)o[0] >> (32 * h)), o1 = (uint32_t)((uint64_t)o[1] >> (32 * h));
-            const uint32_t o2 = (uint32_t)((uint64_t)o[2] >> (32 * h)), o3 = (uint32_t)((uint64_t)o[3] >> (32 * h));
-            const uint32_t x1 = o0 ^ o1, x2 = o2 ^ o3, c1 = o0 & o1, c2 = o2 & o3;
-            const uint32_t b0 = x1 ^ x2, b1 = c1 ^ c2 ^ (x1 & x2), b2 = c1 & c2;
-#pragma unroll
-            for (int g = 0; g < 8; ++g)
-                packed[8 * h + g] = spread_nibble((b0 >> (4 * g)) & 15u) | (spread_nibble((b1 >> (4 * g)) & 15u) << 1) |
-                                    (spread_nibble((b2 >> (4 * g)) & 15u) << 2);
+    for (int h = 0; h < PW / 32; ++h) {
+        const uint32_t o0 = (uint32_t)((uint64_t)o[0] >> (32 * h)), o1 = (uint32_t)((uint64_t)o[1] >> (32 * h));
+        const uint32_t o2 = (uint32_t)((uint64_t)o[2] >> (32 * h)), o3 = (uint32_t)((uint64_t)o[3] >> (32 * h));
+        const uint32_t x1 = o0 ^ o1, x2 = o2 ^ o3, c1 = o0 & o1, c2 = o2 & o3;
+        uint32_t b0 = x1 ^ x2, b1 = c1 ^ c2 ^ (x1 & x2), b2 = c1 & c2;
+#pragma unroll 2
+        for (int g = 0; g < (T::W < 32 ? T::W / 4 : 8); ++g) {
+            const uint32_t word = spread_nibble(b0 & 15u) | (spread_nibble(b1 & 15u) << 1) | (spread_nibble(b2 & 15u) << 2);
+            const uint32_t sum = __reduce_add_sync(kFull, word);
+            if (lane == 0) reinterpret_cast<uint32_t *>(scratch)[8 * h + g] = sum;
+            b0 >>= 4;
+            b1 >>= 4;
+            b2 >>= 4;
         }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < T::W / 4; ++i) {
-        const uint32_t s = __reduce_add_sync(kFull, packed[i]);
-        if (lane == 0) reinterpret_cast<uint32_t *>(scratch)[i] = s;
     }
     __syncwarp();
 
@@ -580,12 +577,28 @@ __device__ __forceinline__ void prefetch_chunk(const Job *jobs, int njobs, const
         asm volatile("prefetch.global.L2 [%0];" ::"l"(q));
 }
 
-// Launch 3, one chunk: G, Z and the plane words again (alpha and w from the analysis), then
+// Chunk c's values into v (the lane's 32) and vx (value 1024 of a 1025-value chunk, lane 31).
+template <int D>
+__device__ __forceinline__ void load_chunk(const Job &job, uint64_t c, int lane, typename Traits<D>::U (&v)[32],
+                                           typename Traits<D>::U &vx) {
+    using U = typename Traits<D>::U;
+    const uint64_t first = c * (uint64_t)job.block;
+    const uint32_t m = (uint32_t)((job.n - first) < job.block ? (job.n - first) : job.block);
+    const uint8_t *src = job.in + first * Traits<D>::S;
+    load_own<D>(src, lane, m, v);
+    vx = (m > 1024u && lane == 31) ? __ldg(reinterpret_cast<const U *>(src) + 1024) : (U)0;
+}
+
+// Launch 2, one chunk: G, Z and the plane words again (alpha and w from the analysis), then
 // the record at its offset.  meta / dense: the chunk's workspace words; size: its record size;
-// rel: its record offset relative to the first record.
-template <int D, bool kWide>
+// rel: its record offset relative to the first record.  With kPre the chunk's values arrive in
+// v / vx, loaded during the previous chunk, and `next` loads the following chunk's into them
+// as soon as the plane words are in shared memory (the register loads then complete while
+// this record is assembled); otherwise the values are loaded here and `next` does nothing.
+template <int D, bool kWide, bool kPre, class Next>
 __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, unsigned long long meta,
-                           unsigned long long dense, uint32_t size, uint64_t rel) {
+                           unsigned long long dense, uint32_t size, uint64_t rel,
+                           typename Traits<D>::U (&v)[32], typename Traits<D>::U &vx, Next &&next) {
     constexpr int kPlOff = EmitLayout<kWide>::kPlOff;
     using T = Traits<D>;
     using U = typename T::U;
@@ -597,14 +610,13 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
     const int alpha_byte = (int)(mb >> 12), beta_hat = (int)((mb >> 7) & 31u), w = (int)(mb & 127u);
     const int alpha = alpha_byte == T::A_SENT ? -1 : alpha_byte;
     const uint64_t rec_off = data_start + rel;
-    if (rec_off + size > job.out_cap) return;    // the job's first chunk reports the capacity error
+    if (rec_off + size > job.out_cap) {          // the job's first chunk reports the capacity error
+        next();
+        return;
+    }
 
     // ---- G, Z and the plane words in shared memory --------------------------------------------
-    const uint8_t *src = job.in + first * T::S;
-    U v[32];
-    load_own<D>(src, lane, m, v);
-    U vx = 0;                                   // value 1024 of a 1025-value chunk
-    if (m > 1024u && lane == 31) vx = __ldg(reinterpret_cast<const U *>(src) + 1024);
+    if constexpr (!kPre) load_chunk<D>(job, c, lane, v, vx);
     const U z1 = to_z<D>(v, vx, alpha, m, lane);
     if (lane == 0) bulk_wait_read();             // the previous record has left the buffer
     __syncwarp();
@@ -621,6 +633,7 @@ __device__ void emit_chunk(const Job &job, uint64_t c, uint8_t *buf, int lane, u
         for (int p = 0; p < (T::W < 32 ? T::W : 32); ++p) *reinterpret_cast<uint32_t *>(dst - p * 128) = a[p];
     }
     __syncwarp();
+    next();                                     // v and vx are free
 
     const uint32_t cols = chunk_cols(m);
     const uint32_t nact = cols / 32u;
@@ -766,42 +779,48 @@ __device__ void finish_job(const Job &job, int lane) {
 
 // Where chunk c's record starts, relative to the first record (Sec. 3.4's size synchronisation,
 // from the analysis' sums): the groups before c's group, the tiles of its group before its tile
-// and the chunks of its tile before it.  Loaded one chunk ahead (every lane), added up when
-// needed.  A group's records take < 2^26 bytes and two tiles and two records < 2^22, so a lane's
-// share stays below 2^32 up to 63 groups per lane (8 M chunks); the warp then adds its 16-bit
-// halves with two 32-bit reductions, and larger shares in 64 bits.
+// and the chunks of its tile before it.  load_info issues the loads one chunk ahead (every lane:
+// one group sum, two tile sums, two sizes) and keeps the raw words, so that nothing waits on them
+// until resolve_info adds them up a chunk later.  A group's records take < 2^26 bytes and a
+// tile's < 2^20, so their low 32-bit words are the sums; with at most 32 groups before c the
+// records before c take < 2^31 bytes (33 * 4096 records of at most 9235 bytes) and one 32-bit
+// reduction adds the lanes' shares.  Beyond that (more than 128 M values at block 1024) the
+// further groups are read when resolving and added in 64 bits.
 struct EmitInfo {
     unsigned long long meta, dense;
-    uint64_t part;                    // this lane's share of the earlier records' bytes
+    uint32_t g0, t0, t1, s0, s1;      // this lane's group sum, two tile sums, two record sizes
     uint32_t size;                    // c's record size
 };
 
 __device__ __forceinline__ EmitInfo load_info(const Job &job, uint64_t c, int lane) {
     const uint64_t nc = job.nchunks;
     const uint32_t *sizes = reinterpret_cast<const uint32_t *>(job.out + 32);
-    const unsigned long long *tsum = job.flags + 2 * nc, *gsum = tsum + tile_count(nc);
+    const uint32_t *tsum = reinterpret_cast<const uint32_t *>(job.flags + 2 * nc);   // low words
+    const uint32_t *gsum = tsum + 2 * tile_count(nc);
+    const uint64_t g = c / kGroup, t = c / kTile, tb = g * (kGroup / kTile), cb = t * kTile;
     EmitInfo e;
     e.meta = job.flags[c];
     e.dense = job.flags[nc + c];
     e.size = sizes[c];
-    const uint64_t g = c / kGroup, t = c / kTile, tb = g * (kGroup / kTile), cb = t * kTile;
-    uint64_t part = 0;
-    for (uint64_t j = (uint64_t)lane; j < g; j += 32) part += gsum[j];
-    if (tb + (uint64_t)lane < t) part += tsum[tb + lane];
-    if (tb + 32u + (uint64_t)lane < t) part += tsum[tb + 32u + lane];
-    if (cb + (uint64_t)lane < c) part += sizes[cb + lane];
-    if (cb + 32u + (uint64_t)lane < c) part += sizes[cb + 32u + lane];
-    e.part = part;
+    e.g0 = (uint64_t)lane < g ? gsum[2 * lane] : 0u;
+    e.t0 = tb + (uint64_t)lane < t ? tsum[2 * (tb + lane)] : 0u;
+    e.t1 = tb + 32u + (uint64_t)lane < t ? tsum[2 * (tb + 32u + lane)] : 0u;
+    e.s0 = cb + (uint64_t)lane < c ? sizes[cb + lane] : 0u;
+    e.s1 = cb + 32u + (uint64_t)lane < c ? sizes[cb + 32u + lane] : 0u;
     return e;
 }
-__device__ __forceinline__ uint64_t resolve_info(const EmitInfo &e) {
-    if (__any_sync(kFull, (e.part >> 32) != 0)) return warp_sum_u64(e.part);
-    const uint32_t p = (uint32_t)e.part;
-    const uint32_t lo = __reduce_add_sync(kFull, p & 0xFFFFu), hi = __reduce_add_sync(kFull, p >> 16);
-    return (uint64_t)lo + ((uint64_t)hi << 16);
+__device__ __forceinline__ uint64_t resolve_info(const Job &job, uint64_t c, const EmitInfo &e, int lane) {
+    const uint32_t p = e.g0 + e.t0 + e.t1 + e.s0 + e.s1;
+    const uint64_t g = c / kGroup;
+    if (g <= 32u) return __reduce_add_sync(kFull, p);
+    const unsigned long long *gsum = job.flags + 2 * job.nchunks + tile_count(job.nchunks);
+    uint64_t part = p;
+    for (uint64_t j = 32u + (uint64_t)lane; j < g; j += 32) part += gsum[j];
+    return warp_sum_u64(part);
 }
 
-// Launch 3: the records (chunks by ticket; the next chunk's values are prefetched into L2).
+// Launch 2: the records (chunks by ticket; the next chunk's values are loaded into registers
+// during the current one, or, in the either-dtype form, prefetched into L2).
 template <bool kWide, int kDt>
 __device__ __forceinline__ void emit_loop(const Job *__restrict__ jobs, int njobs, const Job &s_single,
                                           uint64_t total_chunks, Control *ctl, uint8_t *smem) {
@@ -822,6 +841,11 @@ __device__ __forceinline__ void emit_loop(const Job *__restrict__ jobs, int njob
             }
         }
     }
+    // the FP32 and FP16 forms keep the values of the chunk after the current one in registers
+    // (kPre); the FP64 form has no registers to spare for them
+    constexpr bool kPre = kDt == kDtF32 || kDt == kDtF16;
+    constexpr int DP = kDt == kDtF32 ? kD32 : (kDt == kDtF16 ? kD16 : kD64);
+    typename Traits<DP>::U v[32], vx;
     uint64_t t = ticket_of(take_ticket(ctl, kTicketEmit, lane));
     if (t >= total_chunks) return;
     uint64_t tn = ticket_of(take_ticket(ctl, kTicketEmit, lane));
@@ -829,26 +853,44 @@ __device__ __forceinline__ void emit_loop(const Job *__restrict__ jobs, int njob
     {
         const Job &j0 = job_of(jobs, njobs, s_single, t);
         info = load_info(j0, t - j0.chunk_begin, lane);
+        if constexpr (kPre) load_chunk<DP>(j0, t - j0.chunk_begin, lane, v, vx);
     }
     for (;;) {
-        // the ticket after tn, read at the next iteration; tn's values and words are fetched now
+        // the ticket after tn, read at the next iteration; tn's workspace words are fetched now
         const unsigned long long raw = tn < total_chunks ? take_ticket(ctl, kTicketEmit, lane) : 0ull;
         EmitInfo next{};
         if (tn < total_chunks) {
-            prefetch_chunk(jobs, njobs, s_single, tn, lane);
+            if constexpr (!kPre) prefetch_chunk(jobs, njobs, s_single, tn, lane);
             const Job &jn = job_of(jobs, njobs, s_single, tn);
             next = load_info(jn, tn - jn.chunk_begin, lane);
         }
         const Job &job = job_of(jobs, njobs, s_single, t);
         const uint64_t c = t - job.chunk_begin;
-        const uint64_t rel = resolve_info(info);
+        const uint64_t rel = resolve_info(job, c, info, lane);
         if (c == 0) finish_job(job, lane);
-        if constexpr (kDt == kDtF64) emit_chunk<kD64, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
-        else if constexpr (kDt == kDtF32) emit_chunk<kD32, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
-        else if constexpr (kDt == kDtF16) emit_chunk<kD16, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
-        else if (job.dtype == 0) emit_chunk<kD64, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
-        else if (job.dtype == 1) emit_chunk<kD32, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
-        else emit_chunk<kD16, kWide>(job, c, wbase, lane, info.meta, info.dense, info.size, rel);
+        auto load_next = [&]() {
+            if constexpr (kPre) {
+                if (tn < total_chunks) {
+                    const Job &jn = job_of(jobs, njobs, s_single, tn);
+                    load_chunk<DP>(jn, tn - jn.chunk_begin, lane, v, vx);
+                }
+            }
+        };
+        if constexpr (kPre) {
+            emit_chunk<DP, kWide, true>(job, c, wbase, lane, info.meta, info.dense, info.size, rel, v, vx, load_next);
+        } else if constexpr (kDt == kDtF64) {
+            uint64_t u[32], ux;
+            emit_chunk<kD64, kWide, false>(job, c, wbase, lane, info.meta, info.dense, info.size, rel, u, ux, load_next);
+        } else if (job.dtype == 0) {
+            uint64_t u[32], ux;
+            emit_chunk<kD64, kWide, false>(job, c, wbase, lane, info.meta, info.dense, info.size, rel, u, ux, load_next);
+        } else if (job.dtype == 1) {
+            uint32_t u[32], ux;
+            emit_chunk<kD32, kWide, false>(job, c, wbase, lane, info.meta, info.dense, info.size, rel, u, ux, load_next);
+        } else {
+            uint16_t u[32], ux;
+            emit_chunk<kD16, kWide, false>(job, c, wbase, lane, info.meta, info.dense, info.size, rel, u, ux, load_next);
+        }
         __syncwarp();
         if (tn >= total_chunks) break;
         t = tn;

@@ -658,9 +658,17 @@ __device__ __forceinline__ int find_job(const Job *jobs, int njobs, uint64_t t) 
 
 // Chunk tickets (Control): take_ticket issues lane 0's atomic add and returns its raw result
 // (valid in lane 0 only); ticket_of broadcasts it.  Issuing the atomic a chunk before its result
-// is read hides the atomic's latency behind the current chunk.
+// is read hides the atomic's latency behind the current chunk; the add is predicated on lane 0
+// into a register zeroed beforehand, so no instruction selects between the two and waits for it.
 __device__ __forceinline__ unsigned long long take_ticket(Control *ctl, int which, int lane) {
-    return lane == 0 ? atomicAdd(&ctl->ticket[which], 1ull) : 0ull;
+    unsigned long long r;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %1, 0;\n\tmov.b64 %0, 0;\n\t"
+        "@p atom.global.add.u64 %0, [%2], 1;\n\t}"
+        : "=l"(r)
+        : "r"(lane), "l"(&ctl->ticket[which])
+        : "memory");
+    return r;
 }
 __device__ __forceinline__ uint64_t ticket_of(unsigned long long raw) { return shfl_u64(raw, 0); }
 

@@ -257,3 +257,11 @@ def test_degenerate_series(F, oracle, dtype):
     for name, vals in cases.items():
         for block in (1024, 1025, 64):
             check_parity(F, oracle, vals, block)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_more_than_32_chunk_groups(F, oracle, dtype):
+    """More than 32 groups of 4096 chunks (2-value blocks, 163,842 chunks): record offsets past
+    the first 32 groups are added in 64 bits, and every offset still equals the oracle's."""
+    vals = synth.segments(2 * 40 * 4096 + 3, seed=12, dtype=dtype)
+    check_parity(F, oracle, vals, 2)
