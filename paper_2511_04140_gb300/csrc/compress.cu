@@ -720,8 +720,8 @@ constexpr int kDtF64 = 0, kDtF32 = 1, kDtMixed = 2, kDtF16 = 3;
 // Launch 1: analysis of every chunk (chunks by ticket; the next chunk is copied into
 // the warp's one value buffer while the current one is finished).
 template <int kDt>
-__global__ void __launch_bounds__(32 * kMaxCompressWarps, 1)
-analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
+__device__ __forceinline__ void analyse_loop(const Job *__restrict__ jobs, int njobs, Job single,
+                                             uint64_t total_chunks, Control *ctl) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -757,6 +757,20 @@ analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t tot
         t = tn;
     }
     cp_async_wait_none();
+}
+
+// FP64, FP16 and either-dtype forms (up to 128 registers, 16 warps per SM)
+template <int kDt>
+__global__ void __launch_bounds__(32 * kMaxCompressWarps, 1)
+analyse_kernel(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
+    analyse_loop<kDt>(jobs, njobs, single, total_chunks, ctl);
+}
+
+// FP32 form: held to 96 registers, so that 20 warps fit an SM
+template <int kDt>
+__global__ void __maxnreg__(96)
+analyse_kernel_narrow(const Job *__restrict__ jobs, int njobs, Job single, uint64_t total_chunks, Control *ctl) {
+    analyse_loop<kDt>(jobs, njobs, single, total_chunks, ctl);
 }
 
 // Stream header, stream length and capacity check of one job (one warp): the length is the
@@ -930,9 +944,11 @@ template <int kDt>
 void launch_analyse(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
                     cudaStream_t stream) {
     const int w = g_cta_warps[0], smem = w * kAnalyseWarpBytes;
-    const int g = persistent_grid_of(reinterpret_cast<const void *>(analyse_kernel<kDt>), w, smem, g_ctas_per_sm[0],
-                                     total_chunks);
-    analyse_kernel<kDt><<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
+    void (*kernel)(const Job *, int, Job, uint64_t, Control *);
+    if constexpr (kDt == kDtF32) kernel = analyse_kernel_narrow<kDt>;
+    else kernel = analyse_kernel<kDt>;
+    const int g = persistent_grid_of(reinterpret_cast<const void *>(kernel), w, smem, g_ctas_per_sm[0], total_chunks);
+    kernel<<<g, 32 * w, smem, stream>>>(d_jobs, njobs, single, total_chunks, ctl);
 }
 template <bool kWide, int kDt>
 void launch_emit(const Job *d_jobs, int njobs, const Job &single, uint64_t total_chunks, Control *ctl,
