@@ -834,7 +834,8 @@ __device__ __forceinline__ uint64_t resolve_info(const Job &job, uint64_t c, con
 }
 
 // Launch 2: the records (chunks by ticket; the next chunk's values are loaded into registers
-// during the current one, or, in the either-dtype form, prefetched into L2).
+// during the current one in the FP32 and FP16 forms, prefetched into L2 in the FP64 and
+// either-dtype forms).
 template <bool kWide, int kDt>
 __device__ __forceinline__ void emit_loop(const Job *__restrict__ jobs, int njobs, const Job &s_single,
                                           uint64_t total_chunks, Control *ctl, uint8_t *smem) {
