@@ -14,8 +14,10 @@
 //        group's sums (the size synchronisation of Sec. 3.4), and alpha, beta_hat, w and the
 //        dense-row mask, which go into the workspace;
 //   2. emit: each chunk's record offset from those sums, the values again (straight from
-//      global memory, the next chunk prefetched into L2), G, Z and the bit planes (32x32
-//      register transposes, one 32-bit word per plane: 4 row bytes per lane) from the kept
+//      global memory: FP64 with the next chunk prefetched into L2, FP32 and FP16 with the
+//      next chunk's values loaded into registers during the current record), G, Z and the
+//      bit planes (32x32 register transposes, one 32-bit word per plane: 4 row bytes per
+//      lane) from the kept
 //      alpha and w, the record assembled in shared memory at the output's 16-byte phase, in
 //      place of the plane words it consumes, and sent to its offset with one TMA bulk copy;
 //      the warp of each job's first chunk writes the header and the stream length and checks
